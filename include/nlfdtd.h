@@ -1,0 +1,257 @@
+/*
+ * nlfdtd.h -- C ABI of the GB300 (sm_103a) nonlocal hydrodynamic FDTD library.
+ *
+ * The library advances the 3D Yee FDTD scheme with the linear hydrodynamic
+ * free-electron response of Baxter, Cala Lesina and Ramunno, "Parallel FDTD
+ * modelling of nonlocality in plasmonics" (arXiv 2005.06997):
+ *   - Sec. III, update order f1 (H), f2 (E), f3 (P_CP), f4 (P_f), Table Yee;
+ *   - Eq. NonlocalUpdate (nonlocal Drude) and Eq. GNORUpdate (GNOR), with the
+ *     grad(div P) stencil of Eq. GradDiv, the Pekar condition P_f = 0 outside
+ *     the metal, nonlocal metal only inside the total-field region;
+ *   - Eq. critpointupdate (critical-points bound-electron poles);
+ *   - Eq. discreteamperes for the E update;
+ *   - CPML absorbing boundaries, a TF/SF plane-wave source and running-DFT
+ *     flux monitors for the absorption / scattering / extinction cross
+ *     sections of Sec. V.
+ * One context holds one grid on one GPU.  All functions are plain C; pointers
+ * are host pointers unless the argument says "device".  Every function that
+ * returns int returns NLF_OK (0) or a negative NLF_E_* code; the text of the
+ * last error of a context is available from nlf_last_error().
+ *
+ * Units at the boundary are SI: metres, seconds, rad/s, V/m (E), A/m (H),
+ * C/m^2 (P).  Geometry is given in integer half-cell units: a point with
+ * half-cell coordinates (p0, p1, p2) sits at (p0, p1, p2) * dx / 2.
+ *
+ * Field arrays are [nz][ny][nx] with x fastest.  E_x(i,j,k) sits at
+ * (i+1/2, j, k) dx, E_y at (i, j+1/2, k), E_z at (i, j, k+1/2); H_x at
+ * (i, j+1/2, k+1/2), H_y at (i+1/2, j, k+1/2), H_z at (i+1/2, j+1/2, k)
+ * (Table Yee).  The outer wall of every axis is a PEC at 0 and n cells:
+ * tangential E on index 0 stays zero.
+ *
+ * Thread safety: a context may be used by one host thread at a time;
+ * contexts share nothing.
+ */
+#ifndef NLFDTD_H
+#define NLFDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NLF_OK             0
+#define NLF_E_ARG         (-1)  /* bad argument or inconsistent sizes */
+#define NLF_E_CFL         (-2)  /* S > 1/sqrt(3), or beta dt sqrt(3)/dx > 1 */
+#define NLF_E_GEOMETRY    (-3)  /* metal in the CPML / too close to the TF surface, bad boxes */
+#define NLF_E_OOM         (-4)  /* device allocation failed or bound buffer too small */
+#define NLF_E_CUDA        (-5)  /* a CUDA call failed */
+#define NLF_E_UNSTABLE    (-6)  /* a non-finite field was detected */
+#define NLF_E_TIMEOUT     (-7)  /* nlf_sync gave up waiting */
+#define NLF_E_STATE       (-8)  /* call made in the wrong order */
+#define NLF_E_UNSUPPORTED (-9)  /* valid request outside what this build implements */
+
+#define NLF_BC_PEC       0
+#define NLF_BC_CPML      1      /* CPML of pml_cells, PEC behind it */
+#define NLF_BC_PERIODIC  2      /* accepted by nlf_create only for the CPU oracle; NLF_E_UNSUPPORTED here */
+
+#define NLF_SHAPE_SPHERE     1
+#define NLF_SHAPE_BOX        2
+#define NLF_SHAPE_CUBE_TIPS  3
+
+#define NLF_WAVE_GAUSSIAN    1  /* amplitude exp(-((t-t0)/tau)^2) sin(w0 (t-t0)) */
+#define NLF_WAVE_RAISED_COS  2  /* amplitude [(1-cos(w0 t))/2]^3 for 0 <= t <= 2 pi/w0 (Sec. V) */
+
+#define NLF_FIELD_EX 0
+#define NLF_FIELD_EY 1
+#define NLF_FIELD_EZ 2
+#define NLF_FIELD_HX 3
+#define NLF_FIELD_HY 4
+#define NLF_FIELD_HZ 5
+#define NLF_FIELD_PX 6          /* free-electron polarisation P_f (Sec. III) */
+#define NLF_FIELD_PY 7
+#define NLF_FIELD_PZ 8
+
+#define NLF_MAX_POLES      4
+#define NLF_MAX_MATERIALS  32
+#define NLF_MAX_SHAPES     16
+
+/* Grid (Sec. III, Sec. IV): uniform cubic cells dx, time step dt = S dx / c. */
+typedef struct {
+    int nx, ny, nz;           /* cells, each >= 8 */
+    double dx;                /* m */
+    double courant;           /* S = c dt / dx, 0 < S <= 1/sqrt(3) */
+    int pml_cells;            /* CPML thickness on CPML axes */
+    int boundary[3];          /* NLF_BC_* per axis */
+    double eps_background;    /* relative permittivity of the background */
+} nlf_grid;
+
+/* Material (Sec. II): eps_inf, free electrons (Eq. NonlocDrude / Eq. GNOR)
+ * and critical points (Eq. CritPoint).  wp = 0 means no free electrons;
+ * beta = diff = 0 gives the local Drude model; diff > 0 selects GNOR. */
+typedef struct {
+    double eps_inf;
+    double wp, gamma;         /* rad/s */
+    double beta;              /* m/s */
+    double diff;              /* m^2/s */
+    int n_poles;              /* 0..NLF_MAX_POLES */
+    double A[NLF_MAX_POLES], Omega[NLF_MAX_POLES], Gamma[NLF_MAX_POLES], phi[NLF_MAX_POLES];
+} nlf_material;
+
+/* Shape, integer half-cell units.  The material of an E-site is that of the
+ * first shape (lowest index) containing its point; ties count as inside.
+ *   SPHERE:    |p - center|^2 <= radius^2
+ *   BOX:       |p_a - center_a| <= half[a] for all a
+ *   CUBE_TIPS: cube |p_a - c_a| <= side/2, plus on each of its six face centres
+ *              a square pyramid of base tip_base (even) and height tip_height,
+ *              kept up to tip_cut from the centre, united with a sphere of
+ *              radius tip_radius centred tip_center from the centre on the
+ *              tip axis (the rounded apex). */
+typedef struct {
+    int kind;
+    int material;             /* 1-based index into the material table */
+    int center[3];
+    int radius;
+    int half[3];
+    int side;
+    int tip_base, tip_height, tip_radius, tip_center, tip_cut;
+} nlf_shape;
+
+/* TF/SF plane-wave source (Sec. III: nonlocal metal only in the TF region).
+ * Propagation +z (axis_prop = 2), polarisation x (axis_pol = 0).  The TF box
+ * is given in node indices: E_x(i,j,k) is a total field iff
+ * tf_lo[0] <= i < tf_hi[0], tf_lo[1] <= j <= tf_hi[1], tf_lo[2] <= k <= tf_hi[2]
+ * (in general: its point lies in [2 tf_lo, 2 tf_hi] in half cells). */
+typedef struct {
+    int axis_prop, axis_pol;
+    int tf_lo[3], tf_hi[3];
+    int waveform;             /* NLF_WAVE_* */
+    double w0, tau, t0, amplitude;   /* rad/s, s, s, V/m */
+} nlf_source;
+
+/* Running-DFT monitors: flux boxes in node indices, the absorption box inside
+ * the TF box (one cell clear of its surface), the scattering box outside it
+ * (in the scattered-field region, clear of the CPML).  Samples every
+ * decimate_k steps (E at n dt, H at (n - 1/2) dt), FP64 accumulators. */
+typedef struct {
+    int nf;
+    const double* omega;      /* nf values, rad/s; copied */
+    int abs_lo[3], abs_hi[3];
+    int sca_lo[3], sca_hi[3];
+    int decimate_k;           /* >= 1 */
+    int block_b;              /* samples buffered before accumulation, 1..32 (0 = 16) */
+} nlf_monitors;
+
+/* Sizes and algorithmic traffic of a configured context. */
+typedef struct {
+    long long cells;              /* nx ny nz */
+    long long metal_sites;        /* plasmonic E-sites */
+    long long pole_sites;         /* E-sites with critical-point poles (per pole) */
+    long long bbox_cells;         /* cells of the metal bounding box (with margin) */
+    long long pml_slab_cells;     /* sum over CPML axes of slab cells */
+    long long dft_records;        /* flux-face samples (without the incident record) */
+    double step_bytes;            /* algorithmic HBM bytes of one time step (see DESIGN) */
+    double dt;                    /* s */
+    int gnor, n_poles;
+} nlf_info;
+
+typedef struct nlf_ctx nlf_ctx;
+
+/* Create a context for one grid (validates S and sizes; allocates nothing on
+ * the device).  *out receives the context, to be released by nlf_destroy.
+ * Errors: NLF_E_ARG, NLF_E_CFL, NLF_E_UNSUPPORTED (periodic axes). */
+int nlf_create(const nlf_grid* grid, nlf_ctx** out);
+
+/* Material table (copied), n <= NLF_MAX_MATERIALS.  Coefficients D_1..D_d,
+ * D_G1, D_G2 (Eqs. d1-dd, GNOR) and C_1p..C_p (Eq. critpointupdate) are
+ * formed in FP64 and stored in FP32.  Errors: NLF_E_ARG, NLF_E_CFL
+ * (hydrodynamic stability beta dt sqrt(3) / dx > 1). */
+int nlf_set_materials(nlf_ctx* ctx, const nlf_material* mats, int n);
+
+/* Shapes (copied), voxelised on the device at the first run (integer,
+ * bit-exact).  Replaces any material map.  Errors: NLF_E_ARG. */
+int nlf_set_shapes(nlf_ctx* ctx, const nlf_shape* shapes, int n);
+
+/* Alternative to shapes: a material id per E-site, uint8 [3][nz][ny][nx]
+ * (component-major), host memory, copied.  on_device must be 0. */
+int nlf_set_material_map(nlf_ctx* ctx, const uint8_t* ids3, int on_device);
+
+/* Source (copied).  Errors: NLF_E_ARG, NLF_E_UNSUPPORTED (other axes). */
+int nlf_set_source(nlf_ctx* ctx, const nlf_source* src);
+
+/* Monitors (copied, including omega).  Requires a source.  Errors: NLF_E_ARG,
+ * NLF_E_GEOMETRY. */
+int nlf_set_monitors(nlf_ctx* ctx, const nlf_monitors* mon);
+
+/* Bytes of device state the context needs (for admission by HBM budget).
+ * Valid after materials, shapes/map, source and monitors are set; 0 on error. */
+size_t nlf_state_bytes(const nlf_ctx* ctx);
+
+/* Use caller-owned device memory (e.g. a torch tensor) for the whole state
+ * instead of a library allocation.  dev_ptr must be 256-byte aligned and
+ * stay valid until nlf_destroy.  The memory is cleared on first use.
+ * Errors: NLF_E_ARG, NLF_E_OOM (bytes < nlf_state_bytes), NLF_E_STATE
+ * (state already allocated). */
+int nlf_bind_state(nlf_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Advance `steps` time steps on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  Asynchronous; the first call validates the
+ * geometry, allocates (unless bound), voxelises and uploads.  Runs are
+ * resumable: run(a) then run(b) equals run(a+b) bit for bit.
+ * Errors: NLF_E_STATE, NLF_E_GEOMETRY, NLF_E_OOM, NLF_E_CUDA. */
+int nlf_run(nlf_ctx* ctx, long long steps, void* cuda_stream);
+
+/* Wait for the work queued by nlf_run, polling for at most timeout_ms
+ * (< 0: no limit).  Checks the device error word and the non-finite
+ * watchdog.  Errors: NLF_E_TIMEOUT (work still running; nothing is lost),
+ * NLF_E_UNSTABLE, NLF_E_CUDA. */
+int nlf_sync(nlf_ctx* ctx, int timeout_ms);
+
+/* Copy one field (NLF_FIELD_*) in SI units, FP32, [nz][ny][nx], to dst
+ * (device memory if dst_on_device, else host).  Synchronises the context's
+ * stream.  P outside the metal bounding box is zero. */
+int nlf_get_field(nlf_ctx* ctx, int which, void* dst, int dst_on_device);
+
+/* Copy the voxelised material ids, uint8 [3][nz][ny][nx], to host dst. */
+int nlf_get_voxels(nlf_ctx* ctx, uint8_t* dst);
+
+/* Cross sections in m^2 (FP64, nf values each; any pointer may be NULL),
+ * computed on the device from the FP64 accumulators:
+ *   sigma_abs = -(1/I) sum_abs-box (1/2) Re(E x H*).n dA,
+ *   sigma_sca = +(1/I) sum_sca-box (1/2) Re(E x H*).n dA,
+ *   sigma_ext = sigma_abs + sigma_sca, I = (1/2) Re(E_inc H_inc*) at the
+ *   centre plane of the absorption box.  Uses library scratch in the state. */
+int nlf_get_spectra(nlf_ctx* ctx, double* s_ext, double* s_abs, double* s_sca);
+
+/* Raw accumulators, host dst of 2 * (n_records + 1) * nf * 2 doubles:
+ * [E | H][record][frequency][re, im], SI units, including the K dt factor.
+ * Records are ordered box (absorption, scattering), normal axis a = x, y, z,
+ * low face then high face, term (+E_b H_c, then -E_c H_b with (a,b,c)
+ * cyclic), slower in-plane axis outer; the last record is the incident field. */
+int nlf_get_dft(nlf_ctx* ctx, double* dst);
+long long nlf_num_records(const nlf_ctx* ctx);
+
+/* Checkpoint: copy the whole device state (nlf_state_bytes bytes, including
+ * the step counter and pending DFT samples) to / from host memory. */
+int nlf_save_state(nlf_ctx* ctx, void* host);
+int nlf_load_state(nlf_ctx* ctx, const void* host);
+
+/* Advance n independent contexts, steps[i] each, in one persistent launch per
+ * step group on `cuda_stream`.  status_out[i] receives each context's status
+ * (NLF_OK or NLF_E_*).  All contexts must be configured. */
+int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* cuda_stream, int* status_out);
+
+/* Time index n (E^n, H^{n-1/2} current), sizes, and number of kernels this
+ * context has launched (graph replays count each kernel node). */
+long long nlf_time_index(const nlf_ctx* ctx);
+int nlf_get_info(nlf_ctx* ctx, nlf_info* info);
+long long nlf_kernel_launches(const nlf_ctx* ctx);
+
+const char* nlf_last_error(const nlf_ctx* ctx);
+void nlf_destroy(nlf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
