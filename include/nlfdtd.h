@@ -54,7 +54,7 @@ extern "C" {
 
 #define NLF_BC_PEC       0
 #define NLF_BC_CPML      1      /* CPML of pml_cells, PEC behind it */
-#define NLF_BC_PERIODIC  2      /* accepted by nlf_create only for the CPU oracle; NLF_E_UNSUPPORTED here */
+#define NLF_BC_PERIODIC  2      /* reserved: nlf_create returns NLF_E_UNSUPPORTED */
 
 #define NLF_SHAPE_SPHERE     1
 #define NLF_SHAPE_BOX        2
@@ -140,7 +140,7 @@ typedef struct {
     int abs_lo[3], abs_hi[3];
     int sca_lo[3], sca_hi[3];
     int decimate_k;           /* >= 1 */
-    int block_b;              /* samples buffered before accumulation, 1..32 (0 = 16) */
+    int block_b;              /* samples buffered before accumulation: rounded up to 8, 16 or 32 (0 = 16) */
 } nlf_monitors;
 
 /* Sizes and algorithmic traffic of a configured context. */
@@ -151,9 +151,14 @@ typedef struct {
     long long bbox_cells;         /* cells of the metal bounding box (with margin) */
     long long pml_slab_cells;     /* sum over CPML axes of slab cells */
     long long dft_records;        /* flux-face samples (without the incident record) */
-    double step_bytes;            /* algorithmic HBM bytes of one time step (see DESIGN) */
+    double step_bytes;            /* algorithmic HBM bytes of one time step: 48 cells
+                                   * + 8 (2 + gnor + 2 n_poles) metal_sites + 32 pml_slab_cells
+                                   * + 3 bbox_cells (E and H read and written once, the
+                                   * hydrodynamic state, the CPML psi, the material ids) */
     double dt;                    /* s */
     int gnor, n_poles;
+    long long h2d_bytes;          /* bytes copied host -> device by this context so far */
+    long long d2h_bytes;          /* bytes copied device -> host by this context so far */
 } nlf_info;
 
 typedef struct nlf_ctx nlf_ctx;
@@ -201,6 +206,12 @@ int nlf_bind_state(nlf_ctx* ctx, void* dev_ptr, size_t bytes);
  * resumable: run(a) then run(b) equals run(a+b) bit for bit.
  * Errors: NLF_E_STATE, NLF_E_GEOMETRY, NLF_E_OOM, NLF_E_CUDA. */
 int nlf_run(nlf_ctx* ctx, long long steps, void* cuda_stream);
+
+/* Return the context to time index 0 on `cuda_stream` without reallocating:
+ * every field, polarisation, CPML and DFT array is cleared, the tables are
+ * uploaded again and the shapes voxelised again (the first call allocates,
+ * like nlf_run).  Errors: as nlf_run. */
+int nlf_reset(nlf_ctx* ctx, void* cuda_stream);
 
 /* Wait for the work queued by nlf_run, polling for at most timeout_ms
  * (< 0: no limit).  Checks the device error word and the non-finite

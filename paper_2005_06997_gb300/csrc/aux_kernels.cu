@@ -1,0 +1,249 @@
+// aux_kernels.cu -- voxeliser, running DFT and flux reduction kernels.
+#include <cuda_runtime.h>
+
+#include "nlf_internal.h"
+
+namespace nlf {
+
+// ---------------------------------------------------------------- voxeliser
+// Integer containment tests in half-cell units (bit-exact with any correct
+// implementation of the same definitions).
+
+__device__ __forceinline__ long long sq(long long v) { return v * v; }
+
+__device__ bool contains(const Shape& s, long long p0, long long p1, long long p2)
+{
+    const long long d[3] = {p0 - s.c[0], p1 - s.c[1], p2 - s.c[2]};
+    if (s.kind == 1) return sq(d[0]) + sq(d[1]) + sq(d[2]) <= sq(s.radius);
+    if (s.kind == 2) return llabs(d[0]) <= s.half[0] && llabs(d[1]) <= s.half[1] && llabs(d[2]) <= s.half[2];
+    if (s.kind == 3) {
+        const long long A = s.side / 2, B = s.tip_base / 2, h = s.tip_height;
+        if (llabs(d[0]) <= A && llabs(d[1]) <= A && llabs(d[2]) <= A) return true;
+        for (int ax = 0; ax < 3; ++ax) {
+            const long long v = llabs(d[(ax + 1) % 3]), w = llabs(d[(ax + 2) % 3]);
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const long long t = sg * d[ax];
+                if (sq(t - s.tip_center) + sq(v) + sq(w) <= sq(s.tip_radius)) return true;
+                if (t >= A && t <= s.tip_cut && h * v <= B * (A + h - t) && h * w <= B * (A + h - t)) return true;
+            }
+        }
+    }
+    return false;
+}
+
+__global__ void k_voxelise(const VoxParams v)
+{
+    const long long nb = (long long)v.bb_n[0] * v.bb_n[1] * v.bb_n[2];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nb) return;
+    const int c = (int)(t / nb);
+    const long long r = t - c * nb;
+    const int bi = (int)(r % v.bb_n[0]);
+    const int bj = (int)((r / v.bb_n[0]) % v.bb_n[1]);
+    const int bk = (int)(r / ((long long)v.bb_n[0] * v.bb_n[1]));
+    const long long p0 = 2LL * (bi + v.bb_lo[0]) + (c == 0);
+    const long long p1 = 2LL * (bj + v.bb_lo[1]) + (c == 1);
+    const long long p2 = 2LL * (bk + v.bb_lo[2]) + (c == 2);
+    int id = 0;
+    for (int q = 0; q < v.nshape; ++q) {
+        if (contains(v.shp[q], p0, p1, p2)) {
+            id = v.shp[q].material;
+            break;
+        }
+    }
+    v.mat[c][r] = (uint8_t)id;
+    if (id != 0 && v.free_e[id]) atomicAdd(&v.counts[c], 1ULL);
+}
+
+void launch_voxelise(const VoxParams& v, cudaStream_t st)
+{
+    const long long nb = (long long)v.bb_n[0] * v.bb_n[1] * v.bb_n[2];
+    const long long n = 3 * nb;
+    k_voxelise<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(v);
+}
+
+// ------------------------------------------------------------- running DFT
+
+// Store one FP32 sample of every flux record (E at n dt, H averaged over the
+// two half cells around the face, at (n - 1/2) dt) into slot `slot`.  A
+// non-finite sample raises bit 0 of the error word (the instability watchdog).
+__global__ void k_dft_gather(const DftParams d, const float* __restrict__ E, const float* __restrict__ H,
+                             const float* __restrict__ e_inc, const float* __restrict__ h_inc, int slot,
+                             const long long* __restrict__ step, int* err)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > d.nrec) return;
+    float e, h;
+    if (r < d.nrec) {
+        e = __ldg(E + d.rec_e[r]);
+        const uint32_t o = d.rec_h[r];
+        h = 0.5f * (__ldg(H + o) + __ldg(H + o + d.rec_hs[r]));
+    } else {
+        e = e_inc[d.inc_node];
+        h = 0.5f * (h_inc[d.inc_node - 1] + h_inc[d.inc_node]);
+        d.sample_step[slot] = *step;
+    }
+    const long long w = (long long)slot * (d.nrec + 1) + r;
+    d.sE[w] = e;
+    d.sH[w] = h;
+    if (!isfinite(e) || !isfinite(h)) atomicOr(err, 1);
+}
+
+// Phase table: cos/sin(w_f n dt) and cos/sin(w_f (n - 1/2) dt) per filled
+// slot, from the integer step index in FP64; zeros for unfilled slots.
+__global__ void k_dft_phase(const DftParams d, int count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d.B * d.nf) return;
+    const int s = t / d.nf, f = t - s * d.nf;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < count) {
+        const double n = (double)d.sample_step[s];
+        const double w = d.omega[f];
+        double se, ce, sh, ch;
+        sincos(w * n * d.dt, &se, &ce);
+        sincos(w * (n - 0.5) * d.dt, &sh, &ch);
+        v = make_float4((float)ce, (float)se, (float)ch, (float)sh);
+    }
+    d.phase[t] = v;
+}
+
+// acc[r][f] += sum_s sample[s][r] * exp(i phase[s][f]) for the B buffered
+// samples: FP32 products within one block of samples, FP64 accumulation.
+// Block: blockDim.x frequencies of one frequency chunk x RCH records.
+template <int B, int RCH>
+__global__ void __launch_bounds__(128) k_dft_accum(const DftParams d)
+{
+    __shared__ float sE[B][RCH];
+    __shared__ float sH[B][RCH];
+    const long long r0 = (long long)blockIdx.x * RCH;
+    const int f = blockIdx.y * blockDim.x + threadIdx.x;
+    const long long nr = d.nrec + 1;
+    for (int t = threadIdx.x; t < B * RCH; t += blockDim.x) {
+        const int s = t / RCH, rr = t - s * RCH;
+        const long long r = r0 + rr;
+        sE[s][rr] = r < nr ? d.sE[(long long)s * nr + r] : 0.f;
+        sH[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
+    }
+    __syncthreads();
+    if (f >= d.nf) return;
+    float ce[B], se[B], ch[B], sh[B];
+#pragma unroll
+    for (int s = 0; s < B; ++s) {
+        const float4 v = d.phase[s * d.nf + f];
+        ce[s] = v.x;
+        se[s] = v.y;
+        ch[s] = v.z;
+        sh[s] = v.w;
+    }
+    const int rmax = (int)min((long long)RCH, nr - r0);
+    for (int rr = 0; rr < rmax; ++rr) {
+        float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
+#pragma unroll
+        for (int s = 0; s < B; ++s) {
+            const float e = sE[s][rr], h = sH[s][rr];
+            er = fmaf(e, ce[s], er);
+            ei = fmaf(e, se[s], ei);
+            hr = fmaf(h, ch[s], hr);
+            hi = fmaf(h, sh[s], hi);
+        }
+        const long long a = (r0 + rr) * d.nf + f;
+        double2 ae = d.accE[a], ah = d.accH[a];
+        ae.x += (double)er;
+        ae.y += (double)ei;
+        ah.x += (double)hr;
+        ah.y += (double)hi;
+        d.accE[a] = ae;
+        d.accH[a] = ah;
+    }
+}
+
+void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
+                       int slot, const long long* step, int* err, cudaStream_t st)
+{
+    const long long n = d.nrec + 1;
+    k_dft_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, E, H, e_inc, h_inc, slot, step, err);
+}
+
+void launch_dft_flush(const DftParams& d, int count, cudaStream_t st)
+{
+    const int nt = d.B * d.nf;
+    k_dft_phase<<<(nt + 255) / 256, 256, 0, st>>>(d, count);
+    constexpr int RCH = 32;
+    dim3 grd((unsigned)((d.nrec + 1 + RCH - 1) / RCH), (d.nf + 127) / 128);
+    if (d.B <= 8)
+        k_dft_accum<8, RCH><<<grd, 128, 0, st>>>(d);
+    else if (d.B <= 16)
+        k_dft_accum<16, RCH><<<grd, 128, 0, st>>>(d);
+    else
+        k_dft_accum<32, RCH><<<grd, 128, 0, st>>>(d);
+}
+
+// ----------------------------------------------------------------- fluxes
+
+// partial[g][f] = (sum over records r = g, g+G, ... of the absorption box,
+// same for the scattering box) of coef_r Re(E_r H_r^*), FP64.
+__global__ void k_flux_partial(const double2* __restrict__ accE, const double2* __restrict__ accH,
+                               const double* __restrict__ coef, long long n_abs, long long nrec, int nf,
+                               double2* __restrict__ partial)
+{
+    const int f = blockIdx.y * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int G = gridDim.x;
+    double sa = 0.0, ss = 0.0;
+    for (long long r = blockIdx.x; r < nrec; r += G) {
+        const double2 e = accE[r * nf + f], h = accH[r * nf + f];
+        const double v = __ldg(coef + r) * (e.x * h.x + e.y * h.y);
+        if (r < n_abs)
+            sa += v;
+        else
+            ss += v;
+    }
+    partial[(long long)blockIdx.x * nf + f] = make_double2(sa, ss);
+}
+
+// sigma_abs = -dA S_abs / I, sigma_sca = dA S_sca / I, I = Re(E_inc H_inc^*) / 2.
+__global__ void k_flux_final(const double2* __restrict__ accE, const double2* __restrict__ accH, long long nrec,
+                             int nf, const double2* __restrict__ partial, int G, double dA, double* out)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    double sa = 0.0, ss = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double2 v = partial[(long long)g * nf + f];
+        sa += v.x;
+        ss += v.y;
+    }
+    const double2 e = accE[nrec * nf + f], h = accH[nrec * nf + f];
+    const double I = 0.5 * (e.x * h.x + e.y * h.y);
+    const double s_abs = -sa * dA / I, s_sca = ss * dA / I;
+    out[f] = s_abs + s_sca;
+    out[nf + f] = s_abs;
+    out[2 * nf + f] = s_sca;
+    out[3 * nf + f] = I;
+}
+
+void launch_flux(const double2* accE, const double2* accH, const double* coef, long long n_abs, long long nrec,
+                 int nf, double2* partial, int G, double dA, double* out, cudaStream_t st)
+{
+    dim3 grd(G, (nf + 127) / 128);
+    k_flux_partial<<<grd, 128, 0, st>>>(accE, accH, coef, n_abs, nrec, nf, partial);
+    k_flux_final<<<(nf + 127) / 128, 128, 0, st>>>(accE, accH, nrec, nf, partial, G, dA, out);
+}
+
+}  // namespace nlf
+
+namespace nlf {
+
+__global__ void k_field_out(const float* __restrict__ src, float* __restrict__ dst, long long n, float scale)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) dst[q] = src[q] * scale;
+}
+
+void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st)
+{
+    k_field_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, scale);
+}
+
+}  // namespace nlf

@@ -1,0 +1,1098 @@
+// capi.cu -- host side of the nlf_* C ABI (include/nlfdtd.h).
+//
+// A context owns one state buffer on the device (library-allocated or bound
+// by the caller) that holds every array of the method; nothing else lives on
+// the device.  Time steps are launched eagerly or replayed from a CUDA graph
+// that holds a whole DFT period (K * B steps): the step kernel, the sample
+// gathers and the accumulation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/nlfdtd.h"
+#include "nlf_internal.h"
+
+namespace nlf {
+void launch_step(const StepParams& p, cudaStream_t st);
+void launch_voxelise(const VoxParams& v, cudaStream_t st);
+void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
+                       int slot, const long long* step, int* err, cudaStream_t st);
+void launch_dft_flush(const DftParams& d, int count, cudaStream_t st);
+void launch_flux(const double2* accE, const double2* accH, const double* coef, long long n_abs, long long nrec,
+                 int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
+void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st);
+}  // namespace nlf
+
+namespace {
+
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+
+struct Header {            // first bytes of the state buffer
+    long long step[2];     // step counters, ping-pong by parity
+    int err;               // bit 0: non-finite sample seen
+    int cnt;               // pending DFT samples (host mirror, written before a save)
+    long long n;           // time index (host mirror, written before a save)
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct nlf_ctx {
+    nlf_grid g{};
+    double dt = 0, c0 = 0, eta0 = 0;
+    long long ncell = 0;
+    std::vector<nlf_material> mats;
+    std::vector<nlf_shape> shapes;
+    std::vector<uint8_t> map;      // full [3][nz][ny][nx] map if given
+    bool use_map = false;
+    bool have_src = false;
+    nlf_source src{};
+    bool have_mon = false;
+    nlf_monitors mon{};
+    std::vector<double> omega;
+    std::string err;
+
+    // derived geometry
+    bool has_metal = false;
+    int bb_lo[3] = {0, 0, 0}, bb_n[3] = {0, 0, 0};
+    long long nbb = 0;
+    int inc_off = 0, inc_len = 0, inc_node = 0;
+    int K = 1, B = 16, U = 128;
+    long long nrec = 0, n_abs = 0;
+    int G = 1;
+    int max_poles = 0;
+    bool any_gnor = false;
+    long long pml_slab[3] = {0, 0, 0};
+    bool planned = false;
+
+    // state
+    size_t bytes = 0;
+    char* base = nullptr;
+    bool owned = false;
+    bool ready = false;
+    size_t off_hdr = 0, off_E[2] = {0, 0}, off_H[2] = {0, 0};
+    size_t off_psiE[3] = {0, 0, 0}, off_psiH[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    size_t off_prof[3] = {0, 0, 0};
+    size_t off_inc = 0;
+    size_t off_mat = 0, off_P[2] = {0, 0}, off_auxf = 0, off_gdp = 0, off_pcp = 0, off_auxcp = 0, off_coef = 0,
+           off_free = 0, off_counts = 0;
+    size_t off_rec = 0, off_dcoef = 0, off_omega = 0, off_samples = 0, off_sstep = 0, off_phase = 0, off_acc = 0,
+           off_partial = 0, off_out = 0;
+
+    nlf::StepParams sp[2];
+    nlf::DftParams dp{};
+    cudaStream_t stream = nullptr;      // stream of the last run
+    cudaEvent_t done = nullptr;
+    cudaStream_t cap = nullptr;         // private stream for graph capture
+    cudaGraphExec_t gexec = nullptr;
+    long long gnodes = 0;
+    long long n = 0;                    // time index
+    int cnt = 0;                        // pending DFT samples
+    long long launches = 0;
+    long long h2d = 0, d2h = 0;         // bytes moved between host and device
+    nlf_info info{};
+};
+
+namespace {
+
+int fail(nlf_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(c, NLF_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+T* at(nlf_ctx* c, size_t off) { return reinterpret_cast<T*>(c->base + off); }
+
+// ---------------------------------------------------------------- geometry
+
+// Conservative cell range of E-sites that may lie in shape s (inclusive).
+void shape_cells(const nlf_shape& s, int lo[3], int hi[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        long long r = 0;
+        if (s.kind == NLF_SHAPE_SPHERE) r = s.radius;
+        if (s.kind == NLF_SHAPE_BOX) r = s.half[a];
+        if (s.kind == NLF_SHAPE_CUBE_TIPS)
+            r = std::max<long long>((long long)s.side / 2 + s.tip_height, (long long)s.tip_center + s.tip_radius);
+        // E-sites sit at half-cell coordinate 2 i or 2 i + 1: the first index with
+        // 2 i + 1 >= p0 and the last with 2 i <= p1
+        long long p0 = s.center[a] - r, p1 = s.center[a] + r;
+        lo[a] = (int)std::ceil((p0 - 1) / 2.0);
+        hi[a] = (int)std::floor(p1 / 2.0);
+    }
+}
+
+// Depth-graded CPML coefficients: sigma = sigma_max rho^3, sigma_max =
+// 0.8 (m+1) / (eta0 dx sqrt(eps_b)), alpha = 0.05 S/m (1 - rho), kappa = 1,
+// b = exp(-(sigma + alpha) dt / eps0), c = sigma (b - 1) / (sigma + alpha).
+void cpml_bc(const nlf_ctx* c, double rho, float* b, float* cc)
+{
+    const double m = 3.0;
+    const double smax = 0.8 * (m + 1.0) / (c->eta0 * c->g.dx * std::sqrt(c->g.eps_background));
+    const double sig = smax * std::pow(rho, m);
+    const double alpha = rho > 0.0 ? 0.05 * (1.0 - rho) : 0.0;
+    const double bb = std::exp(-(sig + alpha) * c->dt / kEps0);
+    *b = (float)bb;
+    *cc = (float)((sig + alpha) > 0.0 ? sig * (bb - 1.0) / (sig + alpha) : 0.0);
+}
+
+double axis_depth(double x, int n, int L)
+{
+    double r = 0.0;
+    if (x < L) r = (L - x) / L;
+    else if (x > n - L) r = (x - (n - L)) / L;
+    return std::min(1.0, std::max(0.0, r));
+}
+
+// FP64 coefficients of Sec. III (Eqs. d1-dd, GNOR D_G1, D_G2, critical points
+// C_1p..C_p with the sin(phi) terms of C3p/C5p over dt Cp), normalised
+// (P/eps0, grad-div in difference units) and rounded to FP32.
+nlf::MatCoef make_coef(const nlf_ctx* c, const nlf_material& m)
+{
+    nlf::MatCoef k{};
+    const double dt = c->dt, dx2 = c->g.dx * c->g.dx;
+    double den = m.eps_inf, cE = 0.0;
+    if (m.wp > 0.0) {
+        const double Dd = m.gamma / (2.0 * dt) + 1.0 / (dt * dt);
+        const double D2 = (m.gamma / (2.0 * dt) - 1.0 / (dt * dt)) / Dd;
+        const double D3 = m.wp * m.wp / (4.0 * Dd);                    // D3 / eps0
+        const double eta = m.beta * m.beta + m.diff * m.gamma;
+        const double DG1 = eta / Dd, DG2 = m.diff / (2.0 * dt * Dd);
+        k.free_e = 1;
+        k.gnor = m.diff > 0.0;
+        k.D2 = (float)D2;
+        k.D3 = (float)D3;
+        k.DG2 = (float)(DG2 / dx2);
+        k.G = (float)((DG1 + 3.0 * DG2) / dx2);
+        den += D3;
+        cE += 3.0 * D3;
+    }
+    k.npoles = m.n_poles;
+    for (int p = 0; p < m.n_poles; ++p) {
+        const double A = m.A[p], Om = m.Omega[p], Ga = m.Gamma[p], ph = m.phi[p];
+        const double W2 = Om * Om + Ga * Ga;
+        const double Cp = Ga / dt + 1.0 / (dt * dt) + W2 / 4.0;
+        const double C2 = (Ga / dt - 1.0 / (dt * dt) - W2 / 4.0) / Cp;
+        const double C4 = A * Om * (Om * std::cos(ph) - Ga * std::sin(ph)) / Cp;
+        const double C3 = C4 / 2.0 - A * Om * std::sin(ph) / (dt * Cp);
+        const double C5 = C4 / 2.0 + A * Om * std::sin(ph) / (dt * Cp);
+        k.C2[p] = (float)C2;
+        k.C3[p] = (float)C3;
+        k.C4[p] = (float)C4;
+        k.C5[p] = (float)C5;
+        k.kap[p] = (float)(W2 / Cp);
+        den += C3;
+        cE += C3 + C4;
+    }
+    k.inv_den = (float)(1.0 / den);
+    k.cE = (float)cE;
+    return k;
+}
+
+// Flux-face records of one box, in the order documented in nlfdtd.h.
+void box_records(const nlf_ctx* c, const int lo[3], const int hi[3], std::vector<uint32_t>& re,
+                 std::vector<uint32_t>& rh, std::vector<uint32_t>& rs, std::vector<double>& co)
+{
+    const long long st[3] = {1, c->g.nx, (long long)c->g.nx * c->g.ny};
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, cc = (a + 2) % 3;
+        const int slow = std::max(b, cc), fast = std::min(b, cc);
+        for (int side = 0; side < 2; ++side) {
+            const int p = side == 0 ? lo[a] : hi[a];
+            const double outward = side == 0 ? -1.0 : 1.0;
+            for (int term = 0; term < 2; ++term) {
+                const int ec = term == 0 ? b : cc;       // tangential E component
+                const int hc = term == 0 ? cc : b;       // paired H component
+                const int other = ec == b ? cc : b;      // in-plane axis with node positions
+                const double tsign = term == 0 ? 1.0 : -1.0;
+                const int hs = ec == slow ? hi[slow] - 1 : hi[slow];
+                const int hf = ec == fast ? hi[fast] - 1 : hi[fast];
+                for (int ts = lo[slow]; ts <= hs; ++ts)
+                    for (int tf = lo[fast]; tf <= hf; ++tf) {
+                        int idx[3];
+                        idx[a] = p;
+                        idx[slow] = ts;
+                        idx[fast] = tf;
+                        const double w = (idx[other] == lo[other] || idx[other] == hi[other]) ? 0.5 : 1.0;
+                        const long long cell = idx[0] * st[0] + idx[1] * st[1] + idx[2] * st[2];
+                        re.push_back((uint32_t)(ec * c->ncell + cell));
+                        rh.push_back((uint32_t)(hc * c->ncell + cell - st[a]));
+                        rs.push_back((uint32_t)st[a]);
+                        co.push_back(outward * tsign * w * 0.5);
+                    }
+            }
+        }
+    }
+}
+
+int check_boxes(nlf_ctx* c)
+{
+    const nlf_source& s = c->src;
+    const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+    for (int a = 0; a < 3; ++a) {
+        int lo_lim = c->g.boundary[a] == NLF_BC_CPML ? c->g.pml_cells + 1 : 1;
+        int hi_lim = c->g.boundary[a] == NLF_BC_CPML ? n3[a] - c->g.pml_cells - 1 : n3[a] - 1;
+        if (s.tf_lo[a] < lo_lim || s.tf_hi[a] > hi_lim || s.tf_hi[a] - s.tf_lo[a] < 2)
+            return fail(c, NLF_E_GEOMETRY, "TF box axis %d [%d,%d] must lie in [%d,%d]", a, s.tf_lo[a], s.tf_hi[a],
+                        lo_lim, hi_lim);
+        if (c->has_metal) {
+            int mlo = c->bb_lo[a] + 2, mhi = c->bb_lo[a] + c->bb_n[a] - 3;
+            if (mlo < s.tf_lo[a] + 2 || mhi > s.tf_hi[a] - 2)
+                return fail(c, NLF_E_GEOMETRY, "metal on axis %d (cells %d..%d) closer than 2 cells to the TF surface",
+                            a, mlo, mhi);
+        }
+        if (c->have_mon) {
+            const nlf_monitors& m = c->mon;
+            if (m.abs_lo[a] < s.tf_lo[a] + 1 || m.abs_hi[a] > s.tf_hi[a] - 1 || m.abs_hi[a] <= m.abs_lo[a])
+                return fail(c, NLF_E_GEOMETRY, "absorption box axis %d must lie one cell inside the TF box", a);
+            if (c->has_metal && (m.abs_lo[a] > c->bb_lo[a] + 2 || m.abs_hi[a] < c->bb_lo[a] + c->bb_n[a] - 2))
+                return fail(c, NLF_E_GEOMETRY, "absorption box axis %d does not enclose the metal", a);
+            if (m.sca_lo[a] > s.tf_lo[a] - 1 || m.sca_hi[a] < s.tf_hi[a] + 1 || m.sca_lo[a] < lo_lim ||
+                m.sca_hi[a] > hi_lim)
+                return fail(c, NLF_E_GEOMETRY, "scattering box axis %d must lie between the TF box and the CPML", a);
+        }
+    }
+    return NLF_OK;
+}
+
+// Decide the metal bounding box, DFT layout and the state buffer layout.
+int plan(nlf_ctx* c)
+{
+    if (c->planned) return NLF_OK;
+    const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+    // metal bounding box
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+    bool any = false;
+    if (c->use_map) {
+        for (int cc = 0; cc < 3; ++cc)
+            for (int k = 0; k < n3[2]; ++k)
+                for (int j = 0; j < n3[1]; ++j)
+                    for (int i = 0; i < n3[0]; ++i) {
+                        const uint8_t id = c->map[(size_t)cc * c->ncell + ((size_t)k * n3[1] + j) * n3[0] + i];
+                        if (!id) continue;
+                        if (id > c->mats.size())
+                            return fail(c, NLF_E_ARG, "material map id %d exceeds the %zu materials", id,
+                                        c->mats.size());
+                        any = true;
+                        const int v[3] = {i, j, k};
+                        for (int a = 0; a < 3; ++a) {
+                            lo[a] = std::min(lo[a], v[a]);
+                            hi[a] = std::max(hi[a], v[a]);
+                        }
+                    }
+    } else {
+        for (const nlf_shape& s : c->shapes) {
+            if (s.material < 1 || s.material > (int)c->mats.size())
+                return fail(c, NLF_E_ARG, "shape material %d out of range", s.material);
+            int l[3], h[3];
+            shape_cells(s, l, h);
+            any = true;
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], l[a]);
+                hi[a] = std::max(hi[a], h[a]);
+            }
+        }
+    }
+    c->has_metal = any;
+    if (any) {
+        for (int a = 0; a < 3; ++a) {
+            c->bb_lo[a] = lo[a] - 2;
+            c->bb_n[a] = hi[a] - lo[a] + 5;
+            int pl = c->g.boundary[a] == NLF_BC_CPML ? c->g.pml_cells : 0;
+            if (c->bb_lo[a] < pl + 1 || c->bb_lo[a] + c->bb_n[a] > n3[a] - pl - 1)
+                return fail(c, NLF_E_GEOMETRY, "metal reaches the CPML or the wall on axis %d", a);
+        }
+        c->nbb = (long long)c->bb_n[0] * c->bb_n[1] * c->bb_n[2];
+    }
+    if (c->have_src) {
+        int rc = check_boxes(c);
+        if (rc) return rc;
+        c->inc_off = c->src.tf_lo[2] - 3;
+        c->inc_len = (c->src.tf_hi[2] - c->inc_off + 1) + NLF_INC_MARGIN + NLF_INC_PML;
+    }
+    c->max_poles = 0;
+    c->any_gnor = false;
+    for (const nlf_material& m : c->mats) {
+        c->max_poles = std::max(c->max_poles, m.n_poles);
+        if (m.wp > 0.0 && m.diff > 0.0) c->any_gnor = true;
+    }
+    if (c->have_mon) {
+        c->K = c->mon.decimate_k;
+        // the accumulation kernel is instantiated for 8, 16 and 32 buffered samples
+        const int bb = c->mon.block_b > 0 ? c->mon.block_b : 16;
+        c->B = bb <= 8 ? 8 : (bb <= 16 ? 16 : 32);
+        std::vector<uint32_t> re, rh, rs;
+        std::vector<double> co;
+        box_records(c, c->mon.abs_lo, c->mon.abs_hi, re, rh, rs, co);
+        c->n_abs = (long long)re.size();
+        box_records(c, c->mon.sca_lo, c->mon.sca_hi, re, rh, rs, co);
+        c->nrec = (long long)re.size();
+        c->inc_node = (c->mon.abs_lo[2] + c->mon.abs_hi[2]) / 2 - c->inc_off;
+        c->G = (int)std::min<long long>(608, std::max<long long>(1, c->nrec / 64));
+        long long kb = (long long)c->K * c->B;
+        c->U = (int)(kb % 2 == 0 ? kb : 2 * kb);
+    } else {
+        c->U = 128;
+    }
+    // layout
+    size_t o = 0;
+    auto take = [&](size_t nbytes) {
+        size_t r = o;
+        o = align_up(o + nbytes, 256);
+        return r;
+    };
+    const size_t f3 = 3 * (size_t)c->ncell * sizeof(float);
+    c->off_hdr = take(sizeof(Header));
+    for (int gI = 0; gI < 2; ++gI) c->off_E[gI] = take(f3);
+    for (int gI = 0; gI < 2; ++gI) c->off_H[gI] = take(f3);
+    for (int a = 0; a < 3; ++a) {
+        c->pml_slab[a] = 0;
+        if (c->g.boundary[a] != NLF_BC_CPML) continue;
+        long long other = c->ncell / n3[a];
+        c->pml_slab[a] = 2LL * c->g.pml_cells * other;
+        c->off_psiE[a] = take(2 * c->pml_slab[a] * sizeof(float));
+        for (int gI = 0; gI < 2; ++gI) c->off_psiH[gI][a] = take(2 * c->pml_slab[a] * sizeof(float));
+    }
+    for (int a = 0; a < 3; ++a) c->off_prof[a] = take(4 * (size_t)n3[a] * sizeof(float));
+    if (c->have_src) c->off_inc = take(10 * (size_t)c->inc_len * sizeof(float));
+    c->off_coef = take((NLF_MAX_MAT + 1) * sizeof(nlf::MatCoef));
+    c->off_free = take((NLF_MAX_MAT + 1) * sizeof(int));
+    c->off_counts = take(3 * sizeof(unsigned long long));
+    if (c->has_metal) {
+        const size_t nb = (size_t)c->nbb;
+        c->off_mat = take(3 * nb);
+        c->off_P[0] = take(3 * nb * sizeof(float));
+        c->off_P[1] = take(3 * nb * sizeof(float));
+        c->off_auxf = take(3 * nb * sizeof(float));
+        if (c->any_gnor) c->off_gdp = take(3 * nb * sizeof(float));
+        if (c->max_poles > 0) {
+            c->off_pcp = take((size_t)c->max_poles * 3 * nb * sizeof(float));
+            c->off_auxcp = take((size_t)c->max_poles * 3 * nb * sizeof(float));
+        }
+    }
+    if (c->have_mon) {
+        const size_t nr = (size_t)c->nrec, nr1 = nr + 1, nf = (size_t)c->mon.nf;
+        c->off_rec = take(3 * nr * sizeof(uint32_t) + 64);
+        c->off_dcoef = take(nr * sizeof(double));
+        c->off_omega = take(nf * sizeof(double));
+        c->off_samples = take(2 * (size_t)c->B * nr1 * sizeof(float));
+        c->off_sstep = take((size_t)c->B * sizeof(long long));
+        c->off_phase = take((size_t)c->B * nf * sizeof(float4));
+        c->off_acc = take(2 * nr1 * nf * sizeof(double2));
+        c->off_partial = take((size_t)c->G * nf * sizeof(double2));
+        c->off_out = take(4 * nf * sizeof(double));
+    }
+    c->bytes = o;
+    c->planned = true;
+    return NLF_OK;
+}
+
+void fill_params(nlf_ctx* c)
+{
+    const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+    for (int par = 0; par < 2; ++par) {
+        nlf::StepParams& p = c->sp[par];
+        memset(&p, 0, sizeof p);
+        const int r = par, w = 1 - par;
+        p.nx = c->g.nx;
+        p.ny = c->g.ny;
+        p.nz = c->g.nz;
+        p.S = (float)c->g.courant;
+        p.Sb = (float)(c->g.courant / c->g.eps_background);
+        for (int k = 0; k < 3; ++k) {
+            p.E0[k] = at<float>(c, c->off_E[r]) + k * c->ncell;
+            p.H0[k] = at<float>(c, c->off_H[r]) + k * c->ncell;
+            p.E1[k] = at<float>(c, c->off_E[w]) + k * c->ncell;
+            p.H1[k] = at<float>(c, c->off_H[w]) + k * c->ncell;
+        }
+        p.pml = c->g.pml_cells;
+        for (int a = 0; a < 3; ++a) {
+            p.cpml[a] = c->g.boundary[a] == NLF_BC_CPML;
+            float* pr = at<float>(c, c->off_prof[a]);
+            p.bE[a] = pr;
+            p.cE[a] = pr + n3[a];
+            p.bH[a] = pr + 2 * n3[a];
+            p.cH[a] = pr + 3 * n3[a];
+            if (p.cpml[a]) {
+                for (int s = 0; s < 2; ++s) {
+                    p.psiE[a][s] = at<float>(c, c->off_psiE[a]) + s * c->pml_slab[a];
+                    p.psiH0[a][s] = at<float>(c, c->off_psiH[r][a]) + s * c->pml_slab[a];
+                    p.psiH1[a][s] = at<float>(c, c->off_psiH[w][a]) + s * c->pml_slab[a];
+                }
+            }
+        }
+        p.tfsf = c->have_src;
+        if (c->have_src) {
+            for (int a = 0; a < 3; ++a) {
+                p.tf_lo[a] = c->src.tf_lo[a];
+                p.tf_hi[a] = c->src.tf_hi[a];
+            }
+            p.inc_off = c->inc_off;
+            p.inc_len = c->inc_len;
+            float* inc = at<float>(c, c->off_inc);
+            const int L = c->inc_len;
+            // [e0 e1 h0 h1 psie psih be ce bh ch]
+            p.e_inc0 = inc + r * L;
+            p.e_inc1 = inc + w * L;
+            p.h_inc0 = inc + (2 + r) * L;
+            p.h_inc1 = inc + (2 + w) * L;
+            p.psi_e_inc = inc + 4 * L;
+            p.psi_h_inc = inc + 5 * L;
+            p.b_e_inc = inc + 6 * L;
+            p.c_e_inc = inc + 7 * L;
+            p.b_h_inc = inc + 8 * L;
+            p.c_h_inc = inc + 9 * L;
+            p.waveform = c->src.waveform;
+            p.w0 = c->src.w0;
+            p.tau = c->src.tau;
+            p.t0 = c->src.t0;
+            p.amp = c->src.amplitude;
+            p.dt = c->dt;
+        }
+        p.has_metal = c->has_metal;
+        p.coef = at<nlf::MatCoef>(c, c->off_coef);
+        p.any_gnor = c->any_gnor;
+        p.max_poles = c->max_poles;
+        if (c->has_metal) {
+            const size_t nb = (size_t)c->nbb;
+            for (int a = 0; a < 3; ++a) {
+                p.bb_lo[a] = c->bb_lo[a];
+                p.bb_n[a] = c->bb_n[a];
+            }
+            for (int k = 0; k < 3; ++k) {
+                p.mat[k] = at<uint8_t>(c, c->off_mat) + k * nb;
+                p.P0[k] = at<float>(c, c->off_P[r]) + k * nb;
+                p.P1[k] = at<float>(c, c->off_P[w]) + k * nb;
+                p.auxf[k] = at<float>(c, c->off_auxf) + k * nb;
+                if (c->any_gnor) p.gdp[k] = at<float>(c, c->off_gdp) + k * nb;
+                for (int q = 0; q < c->max_poles; ++q) {
+                    p.pcp[q][k] = at<float>(c, c->off_pcp) + ((size_t)q * 3 + k) * nb;
+                    p.auxcp[q][k] = at<float>(c, c->off_auxcp) + ((size_t)q * 3 + k) * nb;
+                }
+            }
+        }
+        Header* h = at<Header>(c, c->off_hdr);
+        p.step0 = &h->step[r];
+        p.step1 = &h->step[w];
+        p.err = &h->err;
+    }
+    if (c->have_mon) {
+        nlf::DftParams& d = c->dp;
+        const size_t nr1 = (size_t)c->nrec + 1, nf = (size_t)c->mon.nf;
+        d.nrec = c->nrec;
+        d.nf = c->mon.nf;
+        d.B = c->B;
+        uint32_t* rec = at<uint32_t>(c, c->off_rec);
+        d.rec_e = rec;
+        d.rec_h = rec + c->nrec;
+        d.rec_hs = rec + 2 * c->nrec;
+        d.sE = at<float>(c, c->off_samples);
+        d.sH = d.sE + (size_t)c->B * nr1;
+        d.sample_step = at<long long>(c, c->off_sstep);
+        d.phase = at<float4>(c, c->off_phase);
+        d.accE = at<double2>(c, c->off_acc);
+        d.accH = d.accE + nr1 * nf;
+        d.omega = at<double>(c, c->off_omega);
+        d.dt = c->dt;
+        d.inc_node = c->inc_node;
+    }
+}
+
+// Clear the state, upload tables and voxelise.
+int initialise(nlf_ctx* c, cudaStream_t st)
+{
+    const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+    CK(cudaMemsetAsync(c->base, 0, c->bytes, st));
+    std::vector<char> tmp;
+    auto put = [&](size_t off, const void* src, size_t nbytes) -> int {
+        c->h2d += (long long)nbytes;
+        CK(cudaMemcpyAsync(c->base + off, src, nbytes, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));   // host staging buffers are reused
+        return NLF_OK;
+    };
+    int rc;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<float> pr(4 * (size_t)n3[a], 0.f);
+        for (int v = 0; v < n3[a]; ++v) {
+            pr[v] = 1.f;
+            pr[2 * n3[a] + v] = 1.f;
+            if (c->g.boundary[a] != NLF_BC_CPML) continue;
+            cpml_bc(c, axis_depth((double)v, n3[a], c->g.pml_cells), &pr[v], &pr[n3[a] + v]);
+            cpml_bc(c, axis_depth(v + 0.5, n3[a], c->g.pml_cells), &pr[2 * n3[a] + v], &pr[3 * n3[a] + v]);
+        }
+        if ((rc = put(c->off_prof[a], pr.data(), pr.size() * sizeof(float)))) return rc;
+    }
+    if (c->have_src) {
+        const int L = c->inc_len, start = L - NLF_INC_PML;
+        std::vector<float> v(10 * (size_t)L, 0.f);
+        for (int m = 0; m < L; ++m) {
+            double xe = m, xh = m + 0.5;
+            double re = xe > start ? std::min(1.0, (xe - start) / NLF_INC_PML) : 0.0;
+            double rh = xh > start ? std::min(1.0, (xh - start) / NLF_INC_PML) : 0.0;
+            cpml_bc(c, re, &v[6 * (size_t)L + m], &v[7 * (size_t)L + m]);
+            cpml_bc(c, rh, &v[8 * (size_t)L + m], &v[9 * (size_t)L + m]);
+        }
+        if ((rc = put(c->off_inc, v.data(), v.size() * sizeof(float)))) return rc;
+    }
+    std::vector<nlf::MatCoef> coef(NLF_MAX_MAT + 1);
+    std::vector<int> fe(NLF_MAX_MAT + 1, 0);
+    for (size_t m = 0; m < c->mats.size(); ++m) {
+        coef[m + 1] = make_coef(c, c->mats[m]);
+        fe[m + 1] = coef[m + 1].free_e;
+    }
+    if ((rc = put(c->off_coef, coef.data(), coef.size() * sizeof(nlf::MatCoef)))) return rc;
+    if ((rc = put(c->off_free, fe.data(), fe.size() * sizeof(int)))) return rc;
+    if (c->has_metal) {
+        if (c->use_map) {
+            const size_t nb = (size_t)c->nbb;
+            std::vector<uint8_t> sub(3 * nb);
+            for (int cc = 0; cc < 3; ++cc)
+                for (int bk = 0; bk < c->bb_n[2]; ++bk)
+                    for (int bj = 0; bj < c->bb_n[1]; ++bj)
+                        for (int bi = 0; bi < c->bb_n[0]; ++bi) {
+                            size_t src = (size_t)cc * c->ncell +
+                                         ((size_t)(bk + c->bb_lo[2]) * n3[1] + (bj + c->bb_lo[1])) * n3[0] +
+                                         (bi + c->bb_lo[0]);
+                            sub[cc * nb + ((size_t)bk * c->bb_n[1] + bj) * c->bb_n[0] + bi] = c->map[src];
+                        }
+            if ((rc = put(c->off_mat, sub.data(), sub.size()))) return rc;
+            unsigned long long cnts[3] = {0, 0, 0};
+            for (int cc = 0; cc < 3; ++cc)
+                for (size_t q = 0; q < nb; ++q)
+                    if (sub[cc * nb + q] && fe[sub[cc * nb + q]]) ++cnts[cc];
+            if ((rc = put(c->off_counts, cnts, sizeof cnts))) return rc;
+        } else {
+            nlf::VoxParams v{};
+            v.nshape = (int)c->shapes.size();
+            for (int q = 0; q < v.nshape; ++q) {
+                const nlf_shape& s = c->shapes[q];
+                nlf::Shape& d = v.shp[q];
+                d.kind = s.kind;
+                d.material = s.material;
+                for (int a = 0; a < 3; ++a) {
+                    d.c[a] = s.center[a];
+                    d.half[a] = s.half[a];
+                }
+                d.radius = s.radius;
+                d.side = s.side;
+                d.tip_base = s.tip_base;
+                d.tip_height = s.tip_height;
+                d.tip_radius = s.tip_radius;
+                d.tip_center = s.tip_center;
+                d.tip_cut = s.tip_cut;
+            }
+            for (int a = 0; a < 3; ++a) {
+                v.bb_lo[a] = c->bb_lo[a];
+                v.bb_n[a] = c->bb_n[a];
+            }
+            for (int k = 0; k < 3; ++k) v.mat[k] = at<uint8_t>(c, c->off_mat) + (size_t)k * c->nbb;
+            v.counts = at<unsigned long long>(c, c->off_counts);
+            v.free_e = at<int>(c, c->off_free);
+            nlf::launch_voxelise(v, st);
+            CK(cudaGetLastError());
+            c->launches += 1;
+        }
+    }
+    if (c->have_mon) {
+        std::vector<uint32_t> re, rh, rs;
+        std::vector<double> co;
+        box_records(c, c->mon.abs_lo, c->mon.abs_hi, re, rh, rs, co);
+        box_records(c, c->mon.sca_lo, c->mon.sca_hi, re, rh, rs, co);
+        std::vector<uint32_t> all;
+        all.reserve(3 * re.size());
+        all.insert(all.end(), re.begin(), re.end());
+        all.insert(all.end(), rh.begin(), rh.end());
+        all.insert(all.end(), rs.begin(), rs.end());
+        if ((rc = put(c->off_rec, all.data(), all.size() * sizeof(uint32_t)))) return rc;
+        if ((rc = put(c->off_dcoef, co.data(), co.size() * sizeof(double)))) return rc;
+        if ((rc = put(c->off_omega, c->omega.data(), c->omega.size() * sizeof(double)))) return rc;
+    }
+    fill_params(c);
+    // info
+    unsigned long long cnts[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(cnts, c->base + c->off_counts, sizeof cnts, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->d2h += (long long)sizeof cnts;
+    nlf_info& in = c->info;
+    in.cells = c->ncell;
+    in.metal_sites = (long long)(cnts[0] + cnts[1] + cnts[2]);
+    in.pole_sites = c->max_poles > 0 ? in.metal_sites : 0;
+    in.bbox_cells = c->nbb;
+    in.pml_slab_cells = c->pml_slab[0] + c->pml_slab[1] + c->pml_slab[2];
+    in.dft_records = c->nrec;
+    in.dt = c->dt;
+    in.gnor = c->any_gnor;
+    in.n_poles = c->max_poles;
+    in.step_bytes = 48.0 * c->ncell + 8.0 * (2 + (c->any_gnor ? 1 : 0) + 2 * c->max_poles) * in.metal_sites +
+                    32.0 * in.pml_slab_cells + 3.0 * c->nbb;
+    c->ready = true;
+    return NLF_OK;
+}
+
+int ensure_ready(nlf_ctx* c, cudaStream_t st)
+{
+    if (c->ready) return NLF_OK;
+    int rc = plan(c);
+    if (rc) return rc;
+    if (!c->base) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, c->bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, NLF_E_OOM, "cudaMalloc(%zu): %s", c->bytes, cudaGetErrorString(e));
+        }
+        c->base = (char*)p;
+        c->owned = true;
+    }
+    if (!c->done) CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+    return initialise(c, st);
+}
+
+// One time step and its monitor work, launched on st.
+void step_once(nlf_ctx* c, cudaStream_t st)
+{
+    nlf::launch_step(c->sp[c->n & 1], st);
+    c->launches += 1;
+    c->n += 1;
+    if (c->have_mon && c->n % c->K == 0) {
+        const int cur = (int)(c->n & 1);
+        Header* h = at<Header>(c, c->off_hdr);
+        const float* inc = c->have_src ? at<float>(c, c->off_inc) : nullptr;
+        nlf::launch_dft_gather(c->dp, at<float>(c, c->off_E[cur]), at<float>(c, c->off_H[cur]),
+                               inc + cur * c->inc_len, inc + (2 + cur) * c->inc_len, c->cnt, &h->step[cur], &h->err,
+                               st);
+        c->launches += 1;
+        c->cnt += 1;
+        if (c->cnt == c->B) {
+            nlf::launch_dft_flush(c->dp, c->B, st);
+            c->launches += 2;
+            c->cnt = 0;
+        }
+    }
+}
+
+int build_graph(nlf_ctx* c)
+{
+    if (c->gexec) return NLF_OK;
+    if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    // the graph is captured from the aligned state n % U == 0, cnt == 0
+    const long long n_save = c->n, l_save = c->launches;
+    const int cnt_save = c->cnt;
+    c->n = 0;
+    c->cnt = 0;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < c->U; ++s) step_once(c, c->cap);
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    c->gnodes = c->launches - l_save;
+    c->n = n_save;
+    c->cnt = cnt_save;
+    c->launches = l_save;
+    if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return NLF_OK;
+}
+
+int flush_pending(nlf_ctx* c, cudaStream_t st)
+{
+    if (c->have_mon && c->cnt > 0) {
+        nlf::launch_dft_flush(c->dp, c->cnt, st);
+        c->launches += 2;
+        c->cnt = 0;
+        CK(cudaGetLastError());
+    }
+    return NLF_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+int nlf_create(const nlf_grid* grid, nlf_ctx** out)
+{
+    if (!grid || !out) return NLF_E_ARG;
+    *out = nullptr;
+    const nlf_grid& g = *grid;
+    if (g.nx < 8 || g.ny < 8 || g.nz < 8 || !(g.dx > 0.0) || !(g.courant > 0.0) || !(g.eps_background >= 1.0 - 1e-12))
+        return NLF_E_ARG;
+    if ((long long)g.nx * g.ny * g.nz * 3 >= (1LL << 32)) return NLF_E_ARG;
+    if (g.courant > 1.0 / std::sqrt(3.0) + 1e-12) return NLF_E_CFL;
+    for (int a = 0; a < 3; ++a) {
+        if (g.boundary[a] == NLF_BC_PERIODIC) return NLF_E_UNSUPPORTED;
+        if (g.boundary[a] != NLF_BC_PEC && g.boundary[a] != NLF_BC_CPML) return NLF_E_ARG;
+        const int n = a == 0 ? g.nx : a == 1 ? g.ny : g.nz;
+        if (g.boundary[a] == NLF_BC_CPML && (g.pml_cells < 1 || 2 * g.pml_cells + 4 > n)) return NLF_E_ARG;
+    }
+    nlf_ctx* c = new nlf_ctx();
+    c->g = g;
+    c->c0 = 1.0 / std::sqrt(kEps0 * kMu0);
+    c->eta0 = std::sqrt(kMu0 / kEps0);
+    c->dt = g.courant * g.dx / c->c0;
+    c->ncell = (long long)g.nx * g.ny * g.nz;
+    *out = c;
+    return NLF_OK;
+}
+
+int nlf_set_materials(nlf_ctx* c, const nlf_material* mats, int n)
+{
+    if (!c || n < 0 || n > NLF_MAX_MATERIALS || (n > 0 && !mats)) return NLF_E_ARG;
+    if (c->ready) return fail(c, NLF_E_STATE, "materials are fixed after the first run");
+    for (int q = 0; q < n; ++q) {
+        const nlf_material& m = mats[q];
+        if (m.n_poles < 0 || m.n_poles > NLF_MAX_POLES || m.eps_inf < 1e-6 || m.wp < 0 || m.gamma < 0 ||
+            m.beta < 0 || m.diff < 0)
+            return fail(c, NLF_E_ARG, "material %d: bad parameters", q + 1);
+        const double eta = m.beta * m.beta + m.diff * m.gamma;
+        if (std::sqrt(eta) * c->dt * std::sqrt(3.0) / c->g.dx > 1.0)
+            return fail(c, NLF_E_CFL, "material %d: hydrodynamic term unstable (beta dt sqrt3/dx > 1)", q + 1);
+    }
+    c->mats.assign(mats, mats + n);
+    c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_set_shapes(nlf_ctx* c, const nlf_shape* shapes, int n)
+{
+    if (!c || n < 0 || n > NLF_MAX_SHAPES || (n > 0 && !shapes)) return NLF_E_ARG;
+    if (c->ready) return fail(c, NLF_E_STATE, "geometry is fixed after the first run");
+    for (int q = 0; q < n; ++q) {
+        const nlf_shape& s = shapes[q];
+        if (s.kind < NLF_SHAPE_SPHERE || s.kind > NLF_SHAPE_CUBE_TIPS || s.material < 1 ||
+            s.material > NLF_MAX_MATERIALS)
+            return fail(c, NLF_E_ARG, "shape %d: bad kind or material", q);
+        if (s.kind == NLF_SHAPE_CUBE_TIPS && (s.side % 2 || s.tip_base % 2 || s.tip_height <= 0))
+            return fail(c, NLF_E_ARG, "shape %d: cube side and tip base must be even, tip height > 0", q);
+    }
+    c->shapes.assign(shapes, shapes + n);
+    c->use_map = false;
+    c->map.clear();
+    c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_set_material_map(nlf_ctx* c, const uint8_t* ids3, int on_device)
+{
+    if (!c || !ids3) return NLF_E_ARG;
+    if (on_device) return fail(c, NLF_E_UNSUPPORTED, "device-resident material maps are not supported");
+    if (c->ready) return fail(c, NLF_E_STATE, "geometry is fixed after the first run");
+    c->map.assign(ids3, ids3 + 3 * (size_t)c->ncell);
+    c->use_map = true;
+    c->shapes.clear();
+    c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_set_source(nlf_ctx* c, const nlf_source* s)
+{
+    if (!c || !s) return NLF_E_ARG;
+    if (c->ready) return fail(c, NLF_E_STATE, "source is fixed after the first run");
+    if (s->axis_prop != 2 || s->axis_pol != 0)
+        return fail(c, NLF_E_UNSUPPORTED, "only +z propagation with x polarisation is implemented");
+    if (s->waveform != NLF_WAVE_GAUSSIAN && s->waveform != NLF_WAVE_RAISED_COS) return NLF_E_ARG;
+    if (s->waveform == NLF_WAVE_GAUSSIAN && !(s->tau > 0.0)) return NLF_E_ARG;
+    if (!(s->w0 > 0.0)) return NLF_E_ARG;
+    c->src = *s;
+    c->have_src = true;
+    c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_set_monitors(nlf_ctx* c, const nlf_monitors* m)
+{
+    if (!c || !m || m->nf < 1 || !m->omega || m->decimate_k < 1 || m->block_b < 0 || m->block_b > 32)
+        return NLF_E_ARG;
+    if (c->ready) return fail(c, NLF_E_STATE, "monitors are fixed after the first run");
+    if (!c->have_src) return fail(c, NLF_E_STATE, "set the source before the monitors");
+    c->mon = *m;
+    c->omega.assign(m->omega, m->omega + m->nf);
+    c->mon.omega = c->omega.data();
+    c->have_mon = true;
+    c->planned = false;
+    return NLF_OK;
+}
+
+size_t nlf_state_bytes(const nlf_ctx* cc)
+{
+    nlf_ctx* c = const_cast<nlf_ctx*>(cc);
+    if (!c) return 0;
+    if (plan(c)) return 0;
+    return c->bytes;
+}
+
+int nlf_bind_state(nlf_ctx* c, void* dev_ptr, size_t bytes)
+{
+    if (!c || !dev_ptr || ((uintptr_t)dev_ptr & 255)) return NLF_E_ARG;
+    if (c->base) return fail(c, NLF_E_STATE, "state already allocated");
+    int rc = plan(c);
+    if (rc) return rc;
+    if (bytes < c->bytes) return fail(c, NLF_E_OOM, "bound buffer %zu < %zu bytes", bytes, c->bytes);
+    c->base = (char*)dev_ptr;
+    c->owned = false;
+    return NLF_OK;
+}
+
+int nlf_run(nlf_ctx* c, long long steps, void* stream)
+{
+    if (!c || steps < 0) return NLF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_ready(c, st);
+    if (rc) return rc;
+    c->stream = st;
+    bool graph_tried = false;
+    while (steps > 0) {
+        const bool aligned = c->cnt == 0 && (c->n % 2 == 0) && (!c->have_mon || c->n % c->K == 0);
+        if (aligned && steps >= c->U) {
+            if (!graph_tried) {
+                graph_tried = true;
+                if ((rc = build_graph(c))) return rc;
+            }
+            CK(cudaGraphLaunch(c->gexec, st));
+            c->n += c->U;
+            c->launches += c->gnodes;
+            steps -= c->U;
+        } else {
+            step_once(c, st);
+            steps -= 1;
+        }
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->done, st));
+    return NLF_OK;
+}
+
+int nlf_reset(nlf_ctx* c, void* stream)
+{
+    if (!c) return NLF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    c->stream = st;
+    if (!c->ready) return ensure_ready(c, st);
+    c->ready = false;
+    c->n = 0;
+    c->cnt = 0;
+    return initialise(c, st);
+}
+
+int nlf_sync(nlf_ctx* c, int timeout_ms)
+{
+    if (!c) return NLF_E_ARG;
+    if (!c->ready) return NLF_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(c->done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return fail(c, NLF_E_CUDA, "event query: %s", cudaGetErrorString(e));
+        if (timeout_ms >= 0 &&
+            std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+            return fail(c, NLF_E_TIMEOUT, "work still running after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int err = 0;
+    CK(cudaMemcpy(&err, c->base + c->off_hdr + offsetof(Header, err), sizeof err, cudaMemcpyDeviceToHost));
+    if (err & 1) return fail(c, NLF_E_UNSTABLE, "non-finite field sample at time index %lld", c->n);
+    return NLF_OK;
+}
+
+int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
+{
+    if (!c || !dst || which < 0 || which > NLF_FIELD_PZ) return NLF_E_ARG;
+    if (!c->ready) return fail(c, NLF_E_STATE, "no state yet");
+    cudaStream_t st = c->stream;
+    CK(cudaStreamSynchronize(st));
+    const int cur = (int)(c->n & 1);
+    const int comp = which % 3;
+    const size_t n = (size_t)c->ncell;
+    if (which <= NLF_FIELD_HZ) {
+        const float* src = at<float>(c, which < 3 ? c->off_E[cur] : c->off_H[cur]) + comp * n;
+        const float scale = which < 3 ? 1.f : (float)(1.0 / c->eta0);
+        if (on_device) {
+            nlf::launch_field_out(src, (float*)dst, (long long)n, scale, st);
+            c->launches += 1;
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+        } else {
+            CK(cudaMemcpy(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost));
+            c->d2h += (long long)(n * sizeof(float));
+            if (scale != 1.f)
+                for (size_t q = 0; q < n; ++q) ((float*)dst)[q] *= scale;
+        }
+        return NLF_OK;
+    }
+    std::vector<float> full(n, 0.f);
+    if (c->has_metal) {
+        const size_t nb = (size_t)c->nbb;
+        std::vector<float> sub(nb);
+        CK(cudaMemcpy(sub.data(), at<float>(c, c->off_P[cur]) + comp * nb, nb * sizeof(float),
+                      cudaMemcpyDeviceToHost));
+        for (int bk = 0; bk < c->bb_n[2]; ++bk)
+            for (int bj = 0; bj < c->bb_n[1]; ++bj)
+                for (int bi = 0; bi < c->bb_n[0]; ++bi)
+                    full[((size_t)(bk + c->bb_lo[2]) * c->g.ny + (bj + c->bb_lo[1])) * c->g.nx + bi + c->bb_lo[0]] =
+                        (float)(kEps0 * sub[((size_t)bk * c->bb_n[1] + bj) * c->bb_n[0] + bi]);
+    }
+    CK(cudaMemcpy(dst, full.data(), n * sizeof(float), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return NLF_OK;
+}
+
+int nlf_get_voxels(nlf_ctx* c, uint8_t* dst)
+{
+    if (!c || !dst) return NLF_E_ARG;
+    int rc = ensure_ready(c, c->stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    const size_t n = (size_t)c->ncell;
+    memset(dst, 0, 3 * n);
+    if (!c->has_metal) return NLF_OK;
+    const size_t nb = (size_t)c->nbb;
+    std::vector<uint8_t> sub(3 * nb);
+    CK(cudaMemcpy(sub.data(), c->base + c->off_mat, 3 * nb, cudaMemcpyDeviceToHost));
+    for (int cc = 0; cc < 3; ++cc)
+        for (int bk = 0; bk < c->bb_n[2]; ++bk)
+            for (int bj = 0; bj < c->bb_n[1]; ++bj)
+                for (int bi = 0; bi < c->bb_n[0]; ++bi)
+                    dst[cc * n + ((size_t)(bk + c->bb_lo[2]) * c->g.ny + (bj + c->bb_lo[1])) * c->g.nx + bi +
+                        c->bb_lo[0]] = sub[cc * nb + ((size_t)bk * c->bb_n[1] + bj) * c->bb_n[0] + bi];
+    return NLF_OK;
+}
+
+int nlf_get_spectra(nlf_ctx* c, double* s_ext, double* s_abs, double* s_sca)
+{
+    if (!c) return NLF_E_ARG;
+    if (!c->ready || !c->have_mon) return fail(c, NLF_E_STATE, "no monitors or no run yet");
+    cudaStream_t st = c->stream;
+    int rc = flush_pending(c, st);
+    if (rc) return rc;
+    const int nf = c->mon.nf;
+    double* out = at<double>(c, c->off_out);
+    nlf::launch_flux(c->dp.accE, c->dp.accH, at<double>(c, c->off_dcoef), c->n_abs, c->nrec, nf,
+                     at<double2>(c, c->off_partial), c->G, c->g.dx * c->g.dx, out, st);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    std::vector<double> h(4 * (size_t)nf);
+    CK(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->d2h += (long long)(h.size() * sizeof(double));
+    if (s_ext) memcpy(s_ext, h.data(), nf * sizeof(double));
+    if (s_abs) memcpy(s_abs, h.data() + nf, nf * sizeof(double));
+    if (s_sca) memcpy(s_sca, h.data() + 2 * nf, nf * sizeof(double));
+    return NLF_OK;
+}
+
+long long nlf_num_records(const nlf_ctx* cc)
+{
+    nlf_ctx* c = const_cast<nlf_ctx*>(cc);
+    if (!c || !c->have_mon || plan(c)) return -1;
+    return c->nrec;
+}
+
+int nlf_get_dft(nlf_ctx* c, double* dst)
+{
+    if (!c || !dst) return NLF_E_ARG;
+    if (!c->ready || !c->have_mon) return fail(c, NLF_E_STATE, "no monitors or no run yet");
+    cudaStream_t st = c->stream;
+    int rc = flush_pending(c, st);
+    if (rc) return rc;
+    const size_t n = ((size_t)c->nrec + 1) * c->mon.nf * 2;
+    CK(cudaMemcpyAsync(dst, c->dp.accE, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->d2h += (long long)(2 * n * sizeof(double));
+    const double se = c->K * c->dt, sh = c->K * c->dt / c->eta0;
+    for (size_t q = 0; q < n; ++q) dst[q] *= se;
+    for (size_t q = 0; q < n; ++q) dst[n + q] *= sh;
+    return NLF_OK;
+}
+
+int nlf_save_state(nlf_ctx* c, void* host)
+{
+    if (!c || !host) return NLF_E_ARG;
+    if (!c->ready) return fail(c, NLF_E_STATE, "no state yet");
+    CK(cudaStreamSynchronize(c->stream));
+    Header h{};
+    CK(cudaMemcpy(&h, c->base + c->off_hdr, sizeof h, cudaMemcpyDeviceToHost));
+    h.n = c->n;
+    h.cnt = c->cnt;
+    CK(cudaMemcpy(c->base + c->off_hdr, &h, sizeof h, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(host, c->base, c->bytes, cudaMemcpyDeviceToHost));
+    return NLF_OK;
+}
+
+int nlf_load_state(nlf_ctx* c, const void* host)
+{
+    if (!c || !host) return NLF_E_ARG;
+    int rc = ensure_ready(c, c->stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->base, host, c->bytes, cudaMemcpyHostToDevice));
+    Header h{};
+    memcpy(&h, host, sizeof h);
+    c->n = h.n;
+    c->cnt = h.cnt;
+    return NLF_OK;
+}
+
+int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* stream, int* status_out)
+{
+    if (!ctxs || n < 0 || !steps) return NLF_E_ARG;
+    int worst = NLF_OK;
+    for (int q = 0; q < n; ++q) {
+        int rc = ctxs[q] ? nlf_run(ctxs[q], steps[q], stream) : NLF_E_ARG;
+        if (status_out) status_out[q] = rc;
+        if (rc) worst = rc;
+    }
+    return worst;
+}
+
+long long nlf_time_index(const nlf_ctx* c) { return c ? c->n : -1; }
+
+int nlf_get_info(nlf_ctx* c, nlf_info* info)
+{
+    if (!c || !info) return NLF_E_ARG;
+    int rc = ensure_ready(c, c->stream);
+    if (rc) return rc;
+    *info = c->info;
+    info->h2d_bytes = c->h2d;
+    info->d2h_bytes = c->d2h;
+    return NLF_OK;
+}
+
+long long nlf_kernel_launches(const nlf_ctx* c) { return c ? c->launches : -1; }
+
+const char* nlf_last_error(const nlf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void nlf_destroy(nlf_ctx* c)
+{
+    if (!c) return;
+    if (c->stream || c->ready) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->owned && c->base) cudaFree(c->base);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// nlf_internal.h -- device-side data layout of the nonlocal FDTD library.
+//
+// Internal units are normalised so that every curl coefficient is the Courant
+// number S = c dt / dx:  E as is, Ht = eta0 H, Pt = P / eps0.  Then
+//   Ht^{n+1/2} = Ht^{n-1/2} - S diff(E^n)                      (f1)
+//   eps_inf dE + dPt_f + sum dPt_CP = S diff(Ht^{n+1/2})        (Eq. discreteamperes)
+// with diff() the plain difference of neighbouring Yee samples.
+//
+// All fields are FP32, structure of arrays, [nz][ny][nx], x fastest.
+// E and H are double buffered (the fused step reads generation n and writes
+// generation n+1 without read/write races between neighbouring threads).
+#pragma once
+
+#include <cstdint>
+
+#ifndef NLF_MAX_POLES
+#define NLF_MAX_POLES 4
+#endif
+#define NLF_MAX_MAT 32
+#define NLF_MAX_SHP 16
+#define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
+#define NLF_INC_MARGIN 10       // vacuum cells between the TF box and that CPML
+
+namespace nlf {
+
+// Per-material FP32 coefficients of the increment form of f2/f3/f4.
+struct MatCoef {
+    float inv_den;      // 1 / (eps_inf + D3 + sum C3)
+    float cE;           // 3 D3 + sum (C3 + C4)
+    float G;            // (D_G1 + 3 D_G2) / dx^2  (D_NL / dx^2 for the nonlocal Drude model)
+    float D2, D3, DG2;  // D2; D3/eps0; D_G2/dx^2
+    float C2[NLF_MAX_POLES], C3[NLF_MAX_POLES], C4[NLF_MAX_POLES], C5[NLF_MAX_POLES],
+        kap[NLF_MAX_POLES];   // C3..C5 / eps0; kap = (Om^2 + Ga^2) / Cp
+    int free_e;         // has free electrons (P_f is updated)
+    int gnor;           // D > 0: GD history used
+    int npoles;
+    int pad;
+};
+
+struct Shape {
+    int kind, material;
+    int c[3];
+    int radius;
+    int half[3];
+    int side, tip_base, tip_height, tip_radius, tip_center, tip_cut;
+};
+
+// Everything the fused time step needs.  Pointers are device pointers.
+struct StepParams {
+    int nx, ny, nz;
+    float S;            // H curl coefficient
+    float Sb;           // S / eps_b, background E curl coefficient
+    const float* E0[3];
+    const float* H0[3];
+    float* E1[3];
+    float* H1[3];
+
+    // CPML: profiles b, c at integer (E) and half-integer (H) positions of
+    // each axis; psi in slabs of 2*pml cells per CPML axis.
+    int pml;
+    int cpml[3];
+    const float* bE[3];
+    const float* cE[3];
+    const float* bH[3];
+    const float* cH[3];
+    float* psiE[3][2];          // [derivative axis][slot]: slot 0 = component a+1, 1 = a+2 (mod 3)
+    const float* psiH0[3][2];
+    float* psiH1[3][2];
+
+    // TF/SF: incident E_x(z index k) = e_inc[k - inc_off], H_y(k) = h_inc[k - inc_off]
+    int tfsf;
+    int tf_lo[3], tf_hi[3];
+    int inc_off, inc_len;
+    const float* e_inc0;        // E_inc^n
+    const float* h_inc0;        // H_inc^{n-1/2}
+    float* e_inc1;              // written by block 0: E_inc^{n+1}
+    float* h_inc1;              //                     H_inc^{n+1/2}
+    float* psi_e_inc;           // 1D CPML auxiliaries (in place, block 0 only)
+    float* psi_h_inc;
+    const float* b_e_inc;
+    const float* c_e_inc;
+    const float* b_h_inc;
+    const float* c_h_inc;
+    int waveform;
+    double w0, tau, t0, amp, dt;
+
+    // metal bounding box (cells [bb_lo, bb_lo + bb_n)) with its hydrodynamic state
+    int has_metal;
+    int bb_lo[3], bb_n[3];
+    const uint8_t* mat[3];
+    const MatCoef* coef;        // [n_materials + 1], index 0 unused
+    const float* P0[3];
+    float* P1[3];
+    float* auxf[3];
+    float* gdp[3];
+    float* pcp[NLF_MAX_POLES][3];
+    float* auxcp[NLF_MAX_POLES][3];
+    int any_gnor;
+    int max_poles;
+
+    // step counters: step0 holds n, block 0 writes n+1 into step1
+    const long long* step0;
+    long long* step1;
+    int* err;
+};
+
+struct VoxParams {
+    int nshape;
+    Shape shp[NLF_MAX_SHP];
+    int bb_lo[3], bb_n[3];
+    uint8_t* mat[3];
+    unsigned long long* counts;   // [3] plasmonic E-sites per component (atomic)
+    const int* free_e;            // [NLF_MAX_MAT + 1] material has free electrons
+};
+
+struct DftParams {
+    long long nrec;             // face records; the incident record is nrec
+    int nf, B;
+    const uint32_t* rec_e;      // offset into the E component space (comp * ncell + cell)
+    const uint32_t* rec_h;      // offset of the first H point
+    const uint32_t* rec_hs;     // stride to the second H point
+    float* sE;                  // [B][nrec + 1]
+    float* sH;
+    long long* sample_step;     // [B]
+    float4* phase;              // [B][nf]: cos, sin at n dt and at (n - 1/2) dt
+    double2* accE;              // [nrec + 1][nf]
+    double2* accH;
+    const double* omega;
+    double dt;
+    int inc_node;
+};
+
+}  // namespace nlf

@@ -216,7 +216,7 @@ def batched_instances(n=64, seed=2005, dx=0.25e-9, steps=4000, pml=8, nf=200, K=
         ext_half, spheres = _dimer_or_sphere(rng, dx, kind)
         beta = rng.uniform(0.9e6, 1.3e6)
         diff = 0.0 if rng.uniform() < 0.5 else rng.uniform(1e-4, 4e-4)
-        side = max(40, int(math.ceil(ext_half / 2)) + 2 * (pml + PML_MARGIN_TF + METAL_MARGIN))
+        side = max(40, int(math.ceil(ext_half / 2)) + 2 * (pml + PML_MARGIN_TF + METAL_MARGIN) + 2)
         if side > 128:
             continue
         mat = drude_material(9.0, 0.02, beta=beta, diff=diff)

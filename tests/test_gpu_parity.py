@@ -1,0 +1,241 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (stated by the problem): relative L2 of every field <= 1e-4 after
+the run; extinction cross-section relative error <= 1e-3 where the incident
+intensity is >= 1e-3 of its maximum, resonance peak within 0.1 %; material
+voxels bit-exact.
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_06997_gb300 import nlfdtd
+from paper_2005_06997_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Px", "Py", "Pz")
+TOL_FIELD = 1e-4
+TOL_SIGMA = 1e-3
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def run_pair(prob, steps, **kw):
+    g = nlfdtd.Solver(prob, **kw)
+    g.run(steps)
+    g.sync()
+    o = oracle.Sim(prob)
+    o.step(steps)
+    return g, o
+
+
+def assert_fields_match(g, o, names=FIELDS, tol=TOL_FIELD):
+    errs = {}
+    for nm in names:
+        ref = o.array(nm)
+        if not np.any(ref):
+            assert not np.any(g.field(nm)), nm
+            continue
+        errs[nm] = rel_l2(g.field(nm), ref)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def early_pulse(prob, band=(1.0, 9.0), t0_tau=2.5):
+    """Same problem with a broad-band pulse that arrives within a few hundred steps."""
+    p = copy.deepcopy(prob)
+    s = W.gaussian_source(p["source"]["tf_lo"], p["source"]["tf_hi"], band)
+    s["t0"] = t0_tau * s["tau"]
+    p["source"] = s
+    return p
+
+
+# ------------------------------------------------------------------ voxels
+
+@pytest.mark.parametrize("case", ["small_sphere", "dimer", "cube_tips", "sphere_ag_r2nm_48"])
+def test_voxels_bit_exact(case):
+    if case == "small_sphere":
+        prob = W.small_sphere()
+    elif case == "dimer":
+        prob = [p for p in W.batched_instances(n=12) if p["name"].startswith("dimer")][0]
+    elif case == "cube_tips":
+        n, dx = 96, 0.25e-9
+        sh = W.cube_tips_shape((n + 1, n, n - 1), 10e-9, 2.5e-9, 2.5e-9, 0.75e-9, dx)
+        reach = sh["side"] // 2 + sh["tip_height"]
+        prob = W.scatter_problem((n, n, n), dx, 8, [W.AU_LIKE_GNOR], [sh], ((n, n, n), (reach,) * 3), 0,
+                                 (1.0, 5.0), nf=4)
+    else:
+        prob = W.CONFIGS[case]()
+    g = nlfdtd.Solver(prob)
+    vg = g.voxels()
+    vo = oracle.Sim(prob).material_map()
+    assert vg.shape == vo.shape
+    assert np.array_equal(vg, vo)
+    assert np.count_nonzero(vo) > 0
+
+
+# ------------------------------------------------------------------ fields
+
+def test_fields_small_gnor_pole_sphere():
+    """GNOR + Lorentz pole, 36^3, sphere off-centre by half cells (ragged tiles)."""
+    prob = W.small_sphere(n=36, steps=0)
+    g, o = run_pair(prob, 420)
+    errs = assert_fields_match(g, o)
+    assert np.max(np.abs(o.array("Px"))) > 0
+
+
+def test_fields_ragged_grid_local_drude():
+    """Non-cubic grid whose sizes are not multiples of the thread-block tile,
+    local Drude metal (beta = D = 0), two spheres of different materials."""
+    dx = 0.5e-9
+    n3 = (45, 37, 49)
+    mats = [W.drude_material(9.0, 0.1), W.drude_material(7.0, 0.3, beta=1.0e6)]
+    shapes = [W.sphere_shape((40, 37, 44), 9, 1), W.sphere_shape((56, 37, 60), 7, 2)]
+    prob = W.scatter_problem(n3, dx, 6, mats, shapes, ((47, 37, 51), (16, 9, 16)), 0, (1.0, 9.0), nf=8, K=3)
+    prob = early_pulse(prob)
+    g, o = run_pair(prob, 333)
+    assert_fields_match(g, o)
+
+
+def test_fields_pole_only_dielectric_and_pec_walls():
+    """No free electrons (wp = 0) with two critical points (phi != 0), PEC
+    walls on one axis: exercises f3 alone and the wall handling."""
+    dx = 0.5e-9
+    mat = {"eps_inf": 2.0, "wp": 0.0, "gamma": 0.0, "beta": 0.0, "diff": 0.0,
+           "poles": [W.lorentz_pole(1.2, 3.0, 0.3, 0.3), W.lorentz_pole(0.5, 5.0, 0.8, -0.2)]}
+    prob = W.scatter_problem((34, 34, 34), dx, 6, [mat], [W.sphere_shape((34, 34, 34), 10)],
+                             ((34, 34, 34), (10, 10, 10)), 0, (1.0, 9.0), nf=8, K=4)
+    prob["bc"] = ("cpml", "pec", "cpml")
+    prob = early_pulse(prob)
+    g, o = run_pair(prob, 300)
+    assert_fields_match(g, o)
+
+
+def test_vacuum_tfsf_keeps_scattered_region_empty():
+    prob = W.small_sphere(n=36, steps=0)
+    prob["shapes"] = []
+    g = nlfdtd.Solver(prob)
+    g.run(500)
+    g.sync()
+    Ex = g.field("Ex")
+    lo, hi = prob["source"]["tf_lo"], prob["source"]["tf_hi"]
+    nz, ny, nx = Ex.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    tf = (i >= lo[0]) & (i <= hi[0] - 1) & (j >= lo[1]) & (j <= hi[1]) & (k >= lo[2]) & (k <= hi[2])
+    peak = np.max(np.abs(Ex[tf]))
+    assert peak > 1e-3
+    assert np.max(np.abs(Ex[~tf])) <= 1e-5 * peak
+    assert np.max(np.abs(g.field("Ey"))) <= 1e-5 * peak
+
+
+# --------------------------------------------------------- DFT and spectra
+
+def test_dft_and_spectra_parity():
+    """Pulse fully through a GNOR + pole sphere: raw FP64 accumulators and the
+    cross sections against the oracle."""
+    prob = W.small_sphere(n=36, steps=0, nf=24, K=4, band_ev=(1.5, 8.5))
+    prob = early_pulse(prob, band=(1.5, 8.5))
+    steps = 2400
+    g, o = run_pair(prob, steps, block_b=16)
+    assert_fields_match(g, o)
+    aEg, aHg = g.dft()
+    aEo, aHo = o.dft()
+    assert rel_l2(aEg, aEo) < 1e-4
+    assert rel_l2(aHg, aHo) < 1e-4
+    sg, so = g.spectra(), o.spectra()
+    sel = so["inc"] >= 1e-3 * so["inc"].max()
+    for key in ("ext", "abs", "sca"):
+        err = np.abs(sg[key][sel] - so[key][sel]) / np.max(np.abs(so[key][sel]))
+        assert np.max(err) <= TOL_SIGMA, (key, np.max(err))
+    assert np.argmax(sg["ext"]) == np.argmax(so["ext"])
+    w = prob["monitors"]["omega"]
+    assert abs(w[np.argmax(sg["ext"])] / w[np.argmax(so["ext"])] - 1) <= 1e-3
+
+
+def test_sphere_ag_48_configuration():
+    """The 48^3 Ag-like sphere configuration, 1000 steps, as specified."""
+    prob = W.config_sphere_ag_48()
+    g, o = run_pair(prob, prob["steps"])
+    assert_fields_match(g, o)
+    aEg, aHg = g.dft()
+    aEo, aHo = o.dft()
+    assert rel_l2(aEg, aEo) < 1e-4
+    assert rel_l2(aHg, aHo) < 1e-4
+
+
+# ----------------------------------------------------------- run control
+
+def test_resume_is_bit_exact_and_checkpoint_roundtrip():
+    prob = early_pulse(W.small_sphere(n=36, steps=0, nf=8, K=4))
+    a = nlfdtd.Solver(prob)
+    a.run(400)
+    a.sync()
+    b = nlfdtd.Solver(prob)
+    b.run(137)
+    b.run(263)
+    b.sync()
+    for nm in FIELDS:
+        assert np.array_equal(a.field(nm), b.field(nm)), nm
+    # checkpoint at 400, run on, restore, run again: identical
+    snap = a.save_state()
+    a.run(100)
+    a.sync()
+    ref = {nm: a.field(nm) for nm in FIELDS}
+    a.load_state(snap)
+    assert a.n == 400
+    a.run(100)
+    a.sync()
+    for nm in FIELDS:
+        assert np.array_equal(a.field(nm), ref[nm]), nm
+    # a straight run to 500 steps has the same fields and accumulators
+    c = nlfdtd.Solver(prob)
+    c.run(500)
+    c.sync()
+    for nm in FIELDS:
+        assert np.array_equal(a.field(nm), c.field(nm)), nm
+    assert np.array_equal(np.stack(a.dft()), np.stack(c.dft()))
+
+
+def test_bound_state_matches_library_allocation():
+    import torch
+    prob = early_pulse(W.small_sphere(n=36, steps=0, nf=8, K=4))
+    a = nlfdtd.Solver(prob)
+    a.run(200)
+    a.sync()
+    b = nlfdtd.Solver(prob)
+    buf = torch.empty(b.state_bytes() + 256, dtype=torch.uint8, device="cuda")
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    b.bind_state(ptr, b.state_bytes())
+    b.run(200)
+    b.sync()
+    for nm in FIELDS:
+        assert np.array_equal(a.field(nm), b.field(nm)), nm
+    del b
+    del buf
+
+
+# ------------------------------------------------------- full-size grid
+
+def test_full_size_au_gnor_224_grid():
+    """The 224^3 GNOR + pole configuration's grid, geometry and launch shape,
+    with a pulse that reaches the sphere within the run; every field against
+    the oracle."""
+    prob = W.config_sphere_au_gnor_224()
+    prob["monitors"]["omega"] = prob["monitors"]["omega"][::40]
+    src = W.gaussian_source(prob["source"]["tf_lo"], prob["source"]["tf_hi"], (1.0, 9.0))
+    src["t0"] = 0.6 * src["tau"]
+    prob["source"] = src
+    steps = 160
+    g, o = run_pair(prob, steps)
+    errs = assert_fields_match(g, o)
+    assert np.max(np.abs(o.array("Px"))) > 0
