@@ -1,0 +1,150 @@
+// batch.cu -- many independent grids advanced together.
+//
+// A batch step is one persistent launch: a grid sized to the resident
+// capacity of the GPU walks a work list of (instance, tile, z chunk) items of
+// every active instance (heaviest instances first) and runs the same tile
+// code as the single-grid step.  The monitor work of all instances is batched
+// the same way (one gather launch per sample, one phase and one accumulation
+// launch per block of samples).  The host captures a whole DFT period of these
+// launches in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "nlf_internal.h"
+
+namespace nlf {
+
+// The first q with end[q] > w (end: inclusive prefix sums).
+__device__ __forceinline__ int find_inst(const long long* end, int n, long long w)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (end[mid] > w)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// One FP32 sample of every record of every instance into slot `slot`.
+__global__ void k_gather_batch(const BatchDft a, int slot)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = a.rec_end[a.n - 1];
+    if (w >= total) return;
+    const int q = find_inst(a.rec_end, a.n, w);
+    const BatchDftInst& I = a.inst[q];
+    const long long r = w - (q > 0 ? a.rec_end[q - 1] : 0);
+    const int cur = I.base_par ^ a.cur_par;
+    const DftParams& d = I.d;
+    float e, h;
+    if (r < d.nrec) {
+        e = __ldg(I.E[cur] + d.rec_e[r]);
+        const uint32_t o = d.rec_h[r];
+        h = 0.5f * (__ldg(I.H[cur] + o) + __ldg(I.H[cur] + o + d.rec_hs[r]));
+    } else {
+        e = I.e_inc[cur][d.inc_node];
+        h = 0.5f * (I.h_inc[cur][d.inc_node - 1] + I.h_inc[cur][d.inc_node]);
+        d.sample_step[slot] = *I.step[cur];
+    }
+    const long long o = (long long)slot * (d.nrec + 1) + r;
+    d.sE[o] = e;
+    d.sH[o] = h;
+    if (!isfinite(e) || !isfinite(h)) atomicOr(I.err, 1);
+}
+
+__global__ void k_phase_batch(const BatchDft a, int count)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = a.ph_end[a.n - 1];
+    if (w >= total) return;
+    const int q = find_inst(a.ph_end, a.n, w);
+    const DftParams& d = a.inst[q].d;
+    const long long t = w - (q > 0 ? a.ph_end[q - 1] : 0);
+    const int s = (int)(t / d.nf), f = (int)(t - (long long)s * d.nf);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < count) {
+        const double n = (double)d.sample_step[s];
+        const double om = d.omega[f];
+        double se, ce, sh, ch;
+        sincos(om * n * d.dt, &se, &ce);
+        sincos(om * (n - 0.5) * d.dt, &sh, &ch);
+        v = make_float4((float)ce, (float)se, (float)ch, (float)sh);
+    }
+    d.phase[t] = v;
+}
+
+// Same arithmetic as the single-grid accumulation: per record chunk and
+// frequency chunk, FP32 sums over the B samples added into FP64.
+template <int B, int RCH>
+__global__ void __launch_bounds__(128) k_accum_batch(const BatchDft a)
+{
+    __shared__ float sEs[B][RCH];
+    __shared__ float sHs[B][RCH];
+    const long long w = blockIdx.x;
+    const int q = find_inst(a.chunk_end, a.n, w);
+    const DftParams& d = a.inst[q].d;
+    const long long r0 = (w - (q > 0 ? a.chunk_end[q - 1] : 0)) * RCH;
+    const int f = blockIdx.y * blockDim.x + threadIdx.x;
+    const long long nr = d.nrec + 1;
+    for (int t = threadIdx.x; t < B * RCH; t += blockDim.x) {
+        const int s = t / RCH, rr = t - s * RCH;
+        const long long r = r0 + rr;
+        sEs[s][rr] = r < nr ? d.sE[(long long)s * nr + r] : 0.f;
+        sHs[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
+    }
+    __syncthreads();
+    if (f >= d.nf) return;
+    float ce[B], se[B], ch[B], sh[B];
+#pragma unroll
+    for (int s = 0; s < B; ++s) {
+        const float4 v = d.phase[s * d.nf + f];
+        ce[s] = v.x;
+        se[s] = v.y;
+        ch[s] = v.z;
+        sh[s] = v.w;
+    }
+    const int rmax = (int)min((long long)RCH, nr - r0);
+    for (int rr = 0; rr < rmax; ++rr) {
+        float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
+#pragma unroll
+        for (int s = 0; s < B; ++s) {
+            const float e = sEs[s][rr], h = sHs[s][rr];
+            er = fmaf(e, ce[s], er);
+            ei = fmaf(e, se[s], ei);
+            hr = fmaf(h, ch[s], hr);
+            hi = fmaf(h, sh[s], hi);
+        }
+        const long long o = (r0 + rr) * d.nf + f;
+        double2 ae = d.accE[o], ah = d.accH[o];
+        ae.x += (double)er;
+        ae.y += (double)ei;
+        ah.x += (double)hr;
+        ah.y += (double)hi;
+        d.accE[o] = ae;
+        d.accH[o] = ah;
+    }
+}
+
+void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st)
+{
+    k_gather_batch<<<(unsigned)((total_records + 255) / 256), 256, 0, st>>>(a, slot);
+}
+
+void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
+                        int count, cudaStream_t st)
+{
+    k_phase_batch<<<(unsigned)((total_phase + 255) / 256), 256, 0, st>>>(a, count);
+    dim3 grd((unsigned)total_chunks, (max_nf + 127) / 128);
+    if (B <= 8)
+        k_accum_batch<8, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+    else if (B <= 16)
+        k_accum_batch<16, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+    else
+        k_accum_batch<32, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+}
+
+}  // namespace nlf

@@ -13,6 +13,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -29,6 +32,11 @@ void launch_dft_flush(const DftParams& d, int count, cudaStream_t st);
 void launch_flux(const double2* accE, const double2* accH, const double* coef, long long n_abs, long long nrec,
                  int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
 void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st);
+void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
+void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st);
+void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
+                        int count, cudaStream_t st);
+int step_kz(const StepParams& p);
 }  // namespace nlf
 
 namespace {
@@ -728,6 +736,245 @@ int flush_pending(nlf_ctx* c, cudaStream_t st)
     return NLF_OK;
 }
 
+// ------------------------------------------------------------- batching
+
+// A batched segment plan: the device descriptors of one ordered set of
+// instances (and their parities) and the CUDA graph of one DFT period.
+struct BatchPlan {
+    std::vector<nlf_ctx*> ctxs;       // heaviest first
+    std::vector<int> par;             // base parity of each instance
+    char* dev = nullptr;              // descriptors (device)
+    nlf::BatchStep bs{};
+    nlf::BatchDft bd{};
+    long long items = 0, recs = 0, phases = 0, chunks = 0;
+    int max_nf = 0, K = 1, B = 8, U = 128;
+    bool mon = false;
+    int kz = 0;                       // z chunk used for every instance (0: per-instance heuristic)
+    std::vector<int> tried;           // autotuner: candidate z chunks tried so far
+    std::vector<float> tried_ms;
+    cudaGraphExec_t gexec = nullptr;
+    long long gnodes = 0;
+    cudaStream_t cap = nullptr;
+    ~BatchPlan()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap) cudaStreamDestroy(cap);
+        if (dev) cudaFree(dev);
+    }
+};
+
+std::mutex g_batch_mu;
+std::vector<std::unique_ptr<BatchPlan>> g_plans;
+const int kTuneKz[] = {8, 16, 32};
+
+// Build the device descriptors of a plan for z chunk kz (0: heuristic).
+int plan_descriptors(BatchPlan* P, int kz)
+{
+    nlf_ctx* c = P->ctxs[0];
+    const int n = (int)P->ctxs.size();
+    std::vector<nlf::StepParams> params(2 * n);
+    std::vector<nlf::BatchInst> inst(n);
+    std::vector<long long> item_end(n), rec_end(n), ph_end(n), chunk_end(n);
+    std::vector<nlf::BatchDftInst> dinst(n);
+    long long it = 0, rc = 0, ph = 0, ch = 0;
+    P->max_nf = 0;
+    for (int q = 0; q < n; ++q) {
+        nlf_ctx* x = P->ctxs[q];
+        params[2 * q] = x->sp[0];
+        params[2 * q + 1] = x->sp[1];
+        nlf::BatchInst& b = inst[q];
+        b.tiles_x = (x->g.nx + 31) / 32;
+        b.tiles_y = (x->g.ny + 7) / 8;
+        b.kz = kz > 0 ? kz : nlf::step_kz(x->sp[0]);
+        b.chunks = (x->g.nz + b.kz - 1) / b.kz;
+        b.base_par = P->par[q];
+        it += (long long)b.tiles_x * b.tiles_y * b.chunks;
+        item_end[q] = it;
+        if (P->mon) {
+            nlf::BatchDftInst& d = dinst[q];
+            d.d = x->dp;
+            for (int g2 = 0; g2 < 2; ++g2) {
+                d.E[g2] = at<float>(x, x->off_E[g2]);
+                d.H[g2] = at<float>(x, x->off_H[g2]);
+                const float* inc = at<float>(x, x->off_inc);
+                d.e_inc[g2] = inc + g2 * x->inc_len;
+                d.h_inc[g2] = inc + (2 + g2) * x->inc_len;
+                d.step[g2] = &at<Header>(x, x->off_hdr)->step[g2];
+            }
+            d.err = &at<Header>(x, x->off_hdr)->err;
+            d.base_par = P->par[q];
+            rc += x->nrec + 1;
+            ph += (long long)x->B * x->mon.nf;
+            ch += (x->nrec + 1 + NLF_BATCH_RCH - 1) / NLF_BATCH_RCH;
+            P->max_nf = std::max(P->max_nf, x->mon.nf);
+        }
+        rec_end[q] = rc;
+        ph_end[q] = ph;
+        chunk_end[q] = ch;
+    }
+    P->items = it;
+    P->recs = rc;
+    P->phases = ph;
+    P->chunks = ch;
+    size_t o = 0;
+    auto take = [&](size_t nb) {
+        size_t r = o;
+        o = align_up(o + nb, 256);
+        return r;
+    };
+    const size_t o_par = take(params.size() * sizeof(nlf::StepParams));
+    const size_t o_inst = take(inst.size() * sizeof(nlf::BatchInst));
+    const size_t o_item = take(n * sizeof(long long));
+    const size_t o_dinst = take(dinst.size() * sizeof(nlf::BatchDftInst));
+    const size_t o_rec = take(n * sizeof(long long));
+    const size_t o_ph = take(n * sizeof(long long));
+    const size_t o_ch = take(n * sizeof(long long));
+    if (!P->dev) {
+        cudaError_t e = cudaMalloc(&P->dev, o);
+        if (e != cudaSuccess) return fail(c, NLF_E_OOM, "batch descriptors: %s", cudaGetErrorString(e));
+    }
+    std::vector<char> h(o, 0);
+    memcpy(h.data() + o_par, params.data(), params.size() * sizeof(nlf::StepParams));
+    memcpy(h.data() + o_inst, inst.data(), inst.size() * sizeof(nlf::BatchInst));
+    memcpy(h.data() + o_item, item_end.data(), n * sizeof(long long));
+    memcpy(h.data() + o_dinst, dinst.data(), dinst.size() * sizeof(nlf::BatchDftInst));
+    memcpy(h.data() + o_rec, rec_end.data(), n * sizeof(long long));
+    memcpy(h.data() + o_ph, ph_end.data(), n * sizeof(long long));
+    memcpy(h.data() + o_ch, chunk_end.data(), n * sizeof(long long));
+    CK(cudaMemcpy(P->dev, h.data(), o, cudaMemcpyHostToDevice));
+    P->bs.params = reinterpret_cast<const nlf::StepParams*>(P->dev + o_par);
+    P->bs.inst = reinterpret_cast<const nlf::BatchInst*>(P->dev + o_inst);
+    P->bs.item_end = reinterpret_cast<const long long*>(P->dev + o_item);
+    P->bs.n = n;
+    P->bd.inst = reinterpret_cast<const nlf::BatchDftInst*>(P->dev + o_dinst);
+    P->bd.rec_end = reinterpret_cast<const long long*>(P->dev + o_rec);
+    P->bd.ph_end = reinterpret_cast<const long long*>(P->dev + o_ph);
+    P->bd.chunk_end = reinterpret_cast<const long long*>(P->dev + o_ch);
+    P->bd.n = n;
+    P->kz = kz;
+    return NLF_OK;
+}
+
+// Capture one DFT period of batched launches (step, gathers, flushes).
+int plan_graph(BatchPlan* P)
+{
+    nlf_ctx* c = P->ctxs[0];
+    if (P->gexec) {
+        cudaGraphExecDestroy(P->gexec);
+        P->gexec = nullptr;
+    }
+    if (!P->cap) CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    long long nodes = 0;
+    CK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+    int slot = 0;
+    for (int s = 0; s < P->U; ++s) {
+        nlf::BatchStep bs = P->bs;
+        bs.launch_par = s & 1;
+        nlf::launch_step_batch(bs, P->items, P->cap);
+        ++nodes;
+        if (P->mon && (s + 1) % P->K == 0) {
+            nlf::BatchDft bd = P->bd;
+            bd.cur_par = (s + 1) & 1;
+            nlf::launch_gather_batch(bd, P->recs, slot, P->cap);
+            ++nodes;
+            if (++slot == P->B) {
+                nlf::launch_flush_batch(bd, P->phases, P->chunks, P->max_nf, P->B, P->B, P->cap);
+                nodes += 2;
+                slot = 0;
+            }
+        }
+    }
+    cudaError_t e = cudaStreamEndCapture(P->cap, &g);
+    if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    P->gnodes = nodes;
+    return NLF_OK;
+}
+
+double inst_cost(const nlf_ctx* c)
+{
+    return (double)c->ncell + 2.0 * (double)c->nbb;   // metal box cells cost about three times a vacuum cell
+}
+
+BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
+{
+    std::stable_sort(act.begin(), act.end(),
+                     [](const nlf_ctx* a, const nlf_ctx* b) { return inst_cost(a) > inst_cost(b); });
+    std::vector<int> par(act.size());
+    for (size_t q = 0; q < act.size(); ++q) par[q] = (int)(act[q]->n & 1);
+    for (auto& P : g_plans)
+        if (P->ctxs == act && P->par == par) return P.get();
+    std::unique_ptr<BatchPlan> P(new BatchPlan());
+    P->ctxs = act;
+    P->par = par;
+    P->mon = act[0]->have_mon;
+    P->K = act[0]->K;
+    P->B = act[0]->B;
+    P->U = act[0]->U;
+    *rcode = plan_descriptors(P.get(), 0);
+    if (*rcode) return nullptr;
+    *rcode = plan_graph(P.get());
+    if (*rcode) return nullptr;
+    g_plans.push_back(std::move(P));
+    return g_plans.back().get();
+}
+
+// Advance every instance of `act` by one DFT period in batched launches.  The
+// autotuner times the first segments of a plan with each candidate z chunk
+// (every candidate computes the same update; only the work split differs) and
+// keeps the fastest.
+int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int rcode = NLF_OK;
+    BatchPlan* P = find_plan(act, &rcode);
+    if (!P) return rcode;
+    nlf_ctx* c = P->ctxs[0];
+    const bool tuning = P->tried.size() < sizeof(kTuneKz) / sizeof(kTuneKz[0]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tuning) {
+        const int kz = kTuneKz[P->tried.size()];
+        if ((rcode = plan_descriptors(P, kz)) || (rcode = plan_graph(P))) return rcode;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+    }
+    CK(cudaGraphLaunch(P->gexec, st));
+    for (nlf_ctx* x : P->ctxs) x->n += P->U;
+    c->launches += P->gnodes;
+    if (tuning) {
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        P->tried.push_back(P->kz);
+        P->tried_ms.push_back(ms);
+        if (P->tried.size() == sizeof(kTuneKz) / sizeof(kTuneKz[0])) {
+            size_t best = 0;
+            for (size_t q = 1; q < P->tried.size(); ++q)
+                if (P->tried_ms[q] < P->tried_ms[best]) best = q;
+            if ((rcode = plan_descriptors(P, P->tried[best])) || (rcode = plan_graph(P))) return rcode;
+        }
+    }
+    return NLF_OK;
+}
+
+void drop_plans(const nlf_ctx* x)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t q = 0; q < g_plans.size();) {
+        if (std::find(g_plans[q]->ctxs.begin(), g_plans[q]->ctxs.end(), x) != g_plans[q]->ctxs.end())
+            g_plans.erase(g_plans.begin() + q);
+        else
+            ++q;
+    }
+}
+
 }  // namespace
 
 // ===================================================================== ABI
@@ -1057,12 +1304,68 @@ int nlf_load_state(nlf_ctx* c, const void* host)
 
 int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* stream, int* status_out)
 {
-    if (!ctxs || n < 0 || !steps) return NLF_E_ARG;
+    if (!ctxs || n < 0 || n > NLF_MAX_BATCH || !steps) return NLF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> rc(n, NLF_OK);
+    std::vector<long long> rem(n, 0);
+    std::vector<int> batchable;
+    for (int q = 0; q < n; ++q) {
+        nlf_ctx* c = ctxs[q];
+        if (!c || steps[q] < 0) {
+            rc[q] = NLF_E_ARG;
+            continue;
+        }
+        rc[q] = ensure_ready(c, st);
+        if (rc[q]) continue;
+        rem[q] = steps[q];
+        batchable.push_back(q);
+    }
+    // instances join a batched segment when they sit on a DFT period boundary
+    // with the same period as the first one; the others run on their own
+    int K = 0, B = 0, U = 0;
+    bool mon = false;
+    std::vector<int> members;
+    for (int q : batchable) {
+        nlf_ctx* c = ctxs[q];
+        if (members.empty()) {
+            K = c->K;
+            B = c->B;
+            U = c->U;
+            mon = c->have_mon;
+        }
+        const bool fits = c->have_mon == mon && c->K == K && c->B == B && c->U == U && c->cnt == 0 &&
+                          (!mon || c->n % K == 0);
+        if (fits) members.push_back(q);
+    }
+    for (;;) {
+        std::vector<nlf_ctx*> act;
+        for (int q : members)
+            if (rc[q] == NLF_OK && rem[q] >= U) act.push_back(ctxs[q]);
+        if (act.empty()) break;
+        int r = batch_segment(act, st);
+        for (int q : members) {
+            if (rc[q] != NLF_OK || rem[q] < U) continue;
+            if (r) {
+                rc[q] = r;
+                continue;
+            }
+            rem[q] -= U;
+        }
+        if (r) break;
+    }
+    for (int q : batchable) {
+        if (rc[q] == NLF_OK && rem[q] > 0) rc[q] = nlf_run(ctxs[q], rem[q], stream);
+        if (rc[q] == NLF_OK) {
+            nlf_ctx* c = ctxs[q];
+            c->stream = st;
+            cudaError_t e = cudaEventRecord(c->done, st);
+            if (e != cudaSuccess) rc[q] = fail(c, NLF_E_CUDA, "event record: %s", cudaGetErrorString(e));
+        }
+    }
     int worst = NLF_OK;
     for (int q = 0; q < n; ++q) {
-        int rc = ctxs[q] ? nlf_run(ctxs[q], steps[q], stream) : NLF_E_ARG;
-        if (status_out) status_out[q] = rc;
-        if (rc) worst = rc;
+        if (status_out) status_out[q] = rc[q];
+        if (rc[q] && worst == NLF_OK) worst = rc[q];
     }
     return worst;
 }
@@ -1088,6 +1391,7 @@ void nlf_destroy(nlf_ctx* c)
 {
     if (!c) return;
     if (c->stream || c->ready) cudaStreamSynchronize(c->stream);
+    drop_plans(c);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->done) cudaEventDestroy(c->done);

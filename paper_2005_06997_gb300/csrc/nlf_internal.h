@@ -20,6 +20,8 @@
 #define NLF_MAX_SHP 16
 #define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
 #define NLF_INC_MARGIN 10       // vacuum cells between the TF box and that CPML
+#define NLF_MAX_BATCH 256       // instances in one batched launch
+#define NLF_BATCH_RCH 32        // records per block of the batched accumulation
 
 namespace nlf {
 
@@ -128,6 +130,42 @@ struct DftParams {
     const double* omega;
     double dt;
     int inc_node;
+};
+
+// Batched stepping: instance q uses params[2 q + (base_par ^ launch parity)].
+struct BatchInst {
+    int tiles_x, tiles_y, chunks, kz;
+    int base_par;
+    int pad;
+};
+
+struct BatchStep {
+    const StepParams* params;   // [2 n]
+    const BatchInst* inst;      // [n]
+    const long long* item_end;  // [n] inclusive prefix sums of work items
+    int n;
+    int launch_par;
+};
+
+struct BatchDftInst {
+    DftParams d;
+    const float* E[2];
+    const float* H[2];
+    const float* e_inc[2];
+    const float* h_inc[2];
+    const long long* step[2];
+    int* err;
+    int base_par;
+    int pad;
+};
+
+struct BatchDft {
+    const BatchDftInst* inst;   // [n]
+    const long long* rec_end;   // [n] prefix sums of (records + 1)
+    const long long* ph_end;    // [n] prefix sums of B * nf
+    const long long* chunk_end; // [n] prefix sums of record chunks
+    int n;
+    int cur_par;                // generation parity of the fields just written
 };
 
 }  // namespace nlf

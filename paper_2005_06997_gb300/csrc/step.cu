@@ -1,13 +1,14 @@
 // step.cu -- one fused time step of the nonlocal hydrodynamic FDTD scheme.
 //
 // One launch advances (H^{n-1/2}, E^n, P^n) to (H^{n+1/2}, E^{n+1}, P^{n+1})
-// in the order of Sec. III: f1 (H), f2 (E), f3 (P_CP), f4 (P_f).  Every
-// thread owns one cell (i,j,k): it writes H^{n+1/2} and E^{n+1} of that cell.
-// The E update needs H^{n+1/2} of the cells at i-1, j-1, k-1, which another
-// thread owns; instead of a grid-wide barrier the thread recomputes those H
-// values from generation n (E, H and psi_H are double buffered), so the whole
-// step is one launch and each field is read once from HBM per step (the
-// neighbour reads hit L1/L2).
+// in the order of Sec. III: f1 (H), f2 (E), f3 (P_CP), f4 (P_f).  A thread
+// block owns a BX x BY column tile and marches through a chunk of z planes.
+// For plane k it stages E^n of planes k and k+1 (with a one-cell halo) in
+// shared memory, computes H^{n+1/2} of the tile plus the -x / -y halo (the
+// halo H is the only recomputed work), keeps H of plane k-1 in registers,
+// and then updates E, P_CP and P_f of the tile.  E, H and psi_H are double
+// buffered (generation n read, n+1 written), so tiles need no grid-wide
+// barrier; every field crosses HBM once per step apart from the halo.
 //
 // f2/f3/f4 are applied in increment form, algebraically identical to the
 // paper's printed recurrences (Eq. NonlocalUpdate, Eq. GNORUpdate,
@@ -39,6 +40,17 @@ __device__ __forceinline__ bool tf_point(const StepParams& p, int h0, int h1, in
 {
     return h0 >= 2 * p.tf_lo[0] && h0 <= 2 * p.tf_hi[0] && h1 >= 2 * p.tf_lo[1] && h1 <= 2 * p.tf_hi[1] &&
            h2 >= 2 * p.tf_lo[2] && h2 <= 2 * p.tf_hi[2];
+}
+
+// True if cell (i,j,k) or one of its +-1 neighbours lies on the other side
+// of the TF surface, i.e. only for the cells where a TF/SF conversion can apply.
+__device__ __forceinline__ bool near_tf(const StepParams& p, int i, int j, int k)
+{
+    const bool inner = i > p.tf_lo[0] && i < p.tf_hi[0] - 1 && j > p.tf_lo[1] && j < p.tf_hi[1] &&
+                       k > p.tf_lo[2] && k < p.tf_hi[2] - 1;
+    const bool outer = i < p.tf_lo[0] - 1 || i > p.tf_hi[0] || j < p.tf_lo[1] - 1 || j > p.tf_hi[1] ||
+                       k < p.tf_lo[2] - 1 || k > p.tf_hi[2];
+    return !(inner || outer);
 }
 
 __device__ __forceinline__ float e_inc(const StepParams& p, int k)
@@ -73,21 +85,19 @@ __device__ __forceinline__ long long slab_index(const StepParams& p, int a, int 
     return ((long long)l * p.ny + j) * p.nx + i;
 }
 
-// H_C^{n+1/2} at cell (i,j,k); if own, also store it and its psi.
-// (curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2}, (C, A1, A2) cyclic.
+// H_C^{n+1/2} at cell (i,j,k) from the E^n values of its curl; if own, also
+// store it and its psi.  (curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2} with
+// (C, A1, A2) cyclic: a_here, a_next = E_{A2} at idx and idx + e_A1,
+// b_here, b_next = E_{A1} at idx and idx + e_A2 (zero beyond the wall).
 template <int C>
-__device__ __forceinline__ float h_next(const StepParams& p, int i, int j, int k, bool own)
+__device__ __forceinline__ float h_from(const StepParams& p, int i, int j, int k, float a_here, float a_next,
+                                        float b_here, float b_next, bool own)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const int n3[3] = {p.nx, p.ny, p.nz};
     const int ix[3] = {i, j, k};
-    const long long st[3] = {1, (long long)p.nx, (long long)p.nx * p.ny};
-    const long long q = (long long)k * st[2] + (long long)j * st[1] + i;
-    float a_here = ldg(p.E0[A2], q);
-    float a_next = (ix[A1] + 1 < n3[A1]) ? ldg(p.E0[A2], q + st[A1]) : 0.f;
-    float b_here = ldg(p.E0[A1], q);
-    float b_next = (ix[A2] + 1 < n3[A2]) ? ldg(p.E0[A1], q + st[A2]) : 0.f;
-    if (p.tfsf && (A1 == 0 || A2 == 0)) {
+    const long long q = ((long long)k * p.ny + j) * p.nx + i;
+    if ((A1 == 0 || A2 == 0) && p.tfsf && near_tf(p, i, j, k)) {
         // only E_x carries an incident field; convert it across the TF/SF surface
         const int self = tf_point(p, 2 * i + hoff(C, 0), 2 * j + hoff(C, 1), 2 * k + hoff(C, 2));
         if (A2 == 0) {   // a_* are E_x at idx and idx + e_A1
@@ -133,14 +143,14 @@ __device__ __forceinline__ float node_div(const StepParams& p, long long b, long
 // E_C^{n+1} at cell (i,j,k) from H^{n+1/2}: hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1),
 // hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
 template <int C>
-__device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k, float hA2, float hA2m, float hA1,
-                                       float hA1m, float& d_here, bool& d_valid)
+__device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k, float En, float hA2, float hA2m,
+                                       float hA1, float hA1m, float& d_here, bool& d_valid)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const int n3[3] = {p.nx, p.ny, p.nz};
     const int ix[3] = {i, j, k};
     const long long q = ((long long)k * p.ny + j) * p.nx + i;
-    if (p.tfsf && (A1 == 1 || A2 == 1)) {
+    if ((A1 == 1 || A2 == 1) && p.tfsf && near_tf(p, i, j, k)) {
         // only H_y carries an incident field
         const int self = tf_point(p, 2 * i + eoff(C, 0), 2 * j + eoff(C, 1), 2 * k + eoff(C, 2));
         if (A2 == 1) {   // hA2 = H_y(idx), hA2m = H_y(idx - e_A1)
@@ -172,7 +182,6 @@ __device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k,
         t2 += psi;
     }
     const float curl = t1 - t2;
-    const float En = ldg(p.E0[C], q);
     int id = 0;
     long long b = 0, sy = 0, sz = 0;
     if (p.has_metal) {
@@ -268,53 +277,216 @@ __device__ void inc_step(const StepParams& p, int tid, int nt)
     }
 }
 
-__global__ void __launch_bounds__(256) k_step(const StepParams p)
+constexpr int BX = 32, BY = 8;
+
+// Stage E^n of plane kk (tile plus a one-cell halo on every side, zero
+// outside the grid) into shared memory.
+__device__ __forceinline__ void load_plane(const StepParams& p, float (*s)[BY + 2][BX + 2], int x0, int y0, int kk,
+                                           int tid)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    if (i < p.nx && j < p.ny && k < p.nz) {
-        // own H^{n+1/2}
-        const float hx = h_next<0>(p, i, j, k, true);
-        const float hy = h_next<1>(p, i, j, k, true);
-        const float hz = h_next<2>(p, i, j, k, true);
-        float d_here = 0.f;
-        bool d_valid = false;
-        // E_x: needs H_z(j-1), H_y(k-1); updated for j >= 1, k >= 1
-        if (j >= 1 && k >= 1) {
-            e_next<0>(p, i, j, k, hz, h_next<2>(p, i, j - 1, k, false), hy, h_next<1>(p, i, j, k - 1, false),
-                      d_here, d_valid);
-        } else {
-            p.E1[0][((long long)k * p.ny + j) * p.nx + i] = 0.f;
-        }
-        // E_y: needs H_x(k-1), H_z(i-1); updated for i >= 1, k >= 1
-        if (i >= 1 && k >= 1) {
-            e_next<1>(p, i, j, k, hx, h_next<0>(p, i, j, k - 1, false), hz, h_next<2>(p, i - 1, j, k, false),
-                      d_here, d_valid);
-        } else {
-            p.E1[1][((long long)k * p.ny + j) * p.nx + i] = 0.f;
-        }
-        // E_z: needs H_y(i-1), H_x(j-1); updated for i >= 1, j >= 1
-        if (i >= 1 && j >= 1) {
-            e_next<2>(p, i, j, k, hy, h_next<1>(p, i - 1, j, k, false), hx, h_next<0>(p, i, j - 1, k, false),
-                      d_here, d_valid);
-        } else {
-            p.E1[2][((long long)k * p.ny + j) * p.nx + i] = 0.f;
+    constexpr int NT = (BY + 2) * (BX + 2);
+    const bool kin = kk >= 0 && kk < p.nz;
+    const long long base = (long long)kk * p.ny * p.nx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* src = p.E0[c];
+        for (int t = tid; t < NT; t += BX * BY) {
+            const int yy = t / (BX + 2), xx = t - yy * (BX + 2);
+            const int gi = x0 - 1 + xx, gj = y0 - 1 + yy;
+            float v = 0.f;
+            if (kin && gi >= 0 && gi < p.nx && gj >= 0 && gj < p.ny) v = __ldg(src + base + (long long)gj * p.nx + gi);
+            s[c][yy][xx] = v;
         }
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
-        const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-        const int nt = blockDim.x * blockDim.y * blockDim.z;
-        if (p.tfsf) inc_step(p, tid, nt);
+}
+
+// One tile (bx, by) and z chunk bz of the fused step; every thread of the
+// block must call it (it synchronises the block).  The tile (0,0,0) also
+// advances the 1D incident grid and the step counter.
+__device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, int bz, int kz,
+                                          float (*sE)[3][BY + 2][BX + 2],
+                          float (*sH)[BY + 1][BX + 1])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int x0 = bx * BX, y0 = by * BY;
+    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool in = i < p.nx && j < p.ny;
+    const int lx = tx + 1, ly = ty + 1;           // position in the staged E tile
+    float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
+    int cur;
+    if (k0 > 0) {
+        load_plane(p, sE[0], x0, y0, k0 - 1, tid);
+        load_plane(p, sE[1], x0, y0, k0, tid);
+        __syncthreads();
+        if (in) {
+            const int km = k0 - 1;
+            hx_prev = h_from<0>(p, i, j, km, sE[0][2][ly][lx], sE[0][2][ly + 1][lx], sE[0][1][ly][lx],
+                                sE[1][1][ly][lx], false);
+            hy_prev = h_from<1>(p, i, j, km, sE[0][0][ly][lx], sE[1][0][ly][lx], sE[0][2][ly][lx],
+                                sE[0][2][ly][lx + 1], false);
+        }
+        __syncthreads();
+        load_plane(p, sE[0], x0, y0, k0 + 1, tid);
+        cur = 1;
+    } else {
+        load_plane(p, sE[0], x0, y0, k0, tid);
+        load_plane(p, sE[1], x0, y0, k0 + 1, tid);
+        cur = 0;
+    }
+    __syncthreads();
+    for (int k = k0; k < k1; ++k) {
+        const int nx_ = cur ^ 1;
+        float hx = 0.f, hy = 0.f, hz = 0.f;
+        // f1: own H^{n+1/2}
+        if (in) {
+            const float ex = sE[cur][0][ly][lx], ey = sE[cur][1][ly][lx], ez = sE[cur][2][ly][lx];
+            hx = h_from<0>(p, i, j, k, ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
+            hy = h_from<1>(p, i, j, k, ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
+            hz = h_from<2>(p, i, j, k, ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true);
+            sH[0][ly][lx] = hx;
+            sH[1][ly][lx] = hy;
+            sH[2][ly][lx] = hz;
+        }
+        // halo H: H_y, H_z at x0-1 (for E_z, E_y) and H_x, H_z at y0-1 (for E_z, E_x)
+        if (tx == 0 && x0 > 0 && j < p.ny) {
+            const int ih = x0 - 1;
+            sH[1][ly][0] = h_from<1>(p, ih, j, k, sE[cur][0][ly][0], sE[nx_][0][ly][0], sE[cur][2][ly][0],
+                                     sE[cur][2][ly][1], false);
+            sH[2][ly][0] = h_from<2>(p, ih, j, k, sE[cur][1][ly][0], sE[cur][1][ly][1], sE[cur][0][ly][0],
+                                     sE[cur][0][ly + 1][0], false);
+        }
+        if (ty == 0 && y0 > 0 && i < p.nx) {
+            const int jh = y0 - 1;
+            sH[0][0][lx] = h_from<0>(p, i, jh, k, sE[cur][2][0][lx], sE[cur][2][1][lx], sE[cur][1][0][lx],
+                                     sE[nx_][1][0][lx], false);
+            sH[2][0][lx] = h_from<2>(p, i, jh, k, sE[cur][1][0][lx], sE[cur][1][0][lx + 1], sE[cur][0][0][lx],
+                                     sE[cur][0][1][lx], false);
+        }
+        __syncthreads();
+        // f2, f3, f4 on the tile
+        if (in) {
+            float d_here = 0.f;
+            bool d_valid = false;
+            const long long q = ((long long)k * p.ny + j) * p.nx + i;
+            if (j >= 1 && k >= 1)
+                e_next<0>(p, i, j, k, sE[cur][0][ly][lx], hz, sH[2][ly - 1][lx], hy, hy_prev, d_here, d_valid);
+            else
+                p.E1[0][q] = 0.f;
+            if (i >= 1 && k >= 1)
+                e_next<1>(p, i, j, k, sE[cur][1][ly][lx], hx, hx_prev, hz, sH[2][ly][lx - 1], d_here, d_valid);
+            else
+                p.E1[1][q] = 0.f;
+            if (i >= 1 && j >= 1)
+                e_next<2>(p, i, j, k, sE[cur][2][ly][lx], hy, sH[1][ly][lx - 1], hx, sH[0][ly - 1][lx], d_here,
+                          d_valid);
+            else
+                p.E1[2][q] = 0.f;
+        }
+        hx_prev = hx;
+        hy_prev = hy;
+        __syncthreads();
+        if (k + 1 < k1) {
+            load_plane(p, sE[cur], x0, y0, k + 2, tid);
+            __syncthreads();
+        }
+        cur = nx_;
+    }
+    if (bx == 0 && by == 0 && bz == 0) {
+        if (p.tfsf) inc_step(p, tid, BX * BY);
         if (tid == 0) *p.step1 = *p.step0 + 1;
+        __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(BX * BY) k_step(const StepParams p, int kz)
+{
+    __shared__ float sE[2][3][BY + 2][BX + 2];
+    __shared__ float sH[3][BY + 1][BX + 1];
+    step_tile(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sE, sH);
+}
+
+// Find the instance of work item w: the first q with end[q] > w.
+__device__ __forceinline__ int find_inst(const long long* end, int n, long long w)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (end[mid] > w)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(BX * BY) k_step_batch(const BatchStep a)
+{
+    __shared__ float sE[2][3][BY + 2][BX + 2];
+    __shared__ float sH[3][BY + 1][BX + 1];
+    __shared__ StepParams sp;
+    __shared__ long long s_end[NLF_MAX_BATCH];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int q = tid; q < a.n; q += BX * BY) s_end[q] = a.item_end[q];
+    __syncthreads();
+    const long long total = s_end[a.n - 1];
+    int loaded = -1;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        const int q = find_inst(s_end, a.n, w);
+        const BatchInst& I = a.inst[q];
+        if (q != loaded) {
+            __syncthreads();
+            const int par = I.base_par ^ a.launch_par;
+            const int* src = reinterpret_cast<const int*>(&a.params[2 * q + par]);
+            int* dst = reinterpret_cast<int*>(&sp);
+            for (int t = tid; t < (int)(sizeof(StepParams) / sizeof(int)); t += BX * BY) dst[t] = src[t];
+            __syncthreads();
+            loaded = q;
+        }
+        const long long r = w - (q > 0 ? s_end[q - 1] : 0);
+        const long long per_plane = (long long)I.tiles_x * I.tiles_y;
+        const int bz = (int)(r / per_plane);
+        const long long rem = r - bz * per_plane;
+        const int by = (int)(rem / I.tiles_x);
+        const int bx = (int)(rem - (long long)by * I.tiles_x);
+        step_tile(sp, bx, by, bz, I.kz, sE, sH);
+    }
+}
+
+int batch_blocks()
+{
+    static int nb = 0;
+    if (nb == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_batch, BX * BY, 0);
+        nb = sms * (per > 0 ? per : 1);
+    }
+    return nb;
+}
+
+void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st)
+{
+    const long long g = total_items < batch_blocks() ? total_items : batch_blocks();
+    k_step_batch<<<(unsigned)g, dim3(BX, BY, 1), 0, st>>>(a);
+}
+
+int step_kz(const StepParams& p)
+{
+    // z chunk: enough blocks for several waves over 152 SMs, few chunk prologues
+    const long long tiles = (long long)((p.nx + BX - 1) / BX) * ((p.ny + BY - 1) / BY);
+    int kz = 32;
+    while (kz > 8 && tiles * ((p.nz + kz - 1) / kz) < 4 * 152 * 4) kz /= 2;
+    return kz;
 }
 
 void launch_step(const StepParams& p, cudaStream_t st)
 {
-    dim3 blk(32, 4, 2);
-    dim3 grd((p.nx + 31) / 32, (p.ny + 3) / 4, (p.nz + 1) / 2);
-    k_step<<<grd, blk, 0, st>>>(p);
+    const int kz = step_kz(p);
+    dim3 blk(BX, BY, 1);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
+    k_step<<<grd, blk, 0, st>>>(p, kz);
 }
 
 }  // namespace nlf

@@ -1,0 +1,103 @@
+"""Batched stepping (nlf_batch_run): many uneven grids in one persistent launch
+per time step, against the same grids run alone and against the oracle."""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_06997_gb300 import nlfdtd
+from paper_2005_06997_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VECTORS = {"E": ("Ex", "Ey", "Ez"), "H": ("Hx", "Hy", "Hz"), "P": ("Px", "Py", "Pz")}
+
+
+def vec_err(a_fields, b_fields):
+    out = {}
+    for vec, comps in VECTORS.items():
+        num = math.sqrt(sum(np.sum((a_fields[c].astype(np.float64) - b_fields[c]) ** 2) for c in comps))
+        den = math.sqrt(sum(np.sum(np.asarray(b_fields[c], dtype=np.float64) ** 2) for c in comps))
+        out[vec] = num / den if den > 0 else num
+    return out
+
+
+def fields(s):
+    return {c: s.field(c) for comps in VECTORS.values() for c in comps}
+
+
+def instances(n, steps, nf=16):
+    out = []
+    for p in W.batched_instances(n=n, nf=nf, steps=steps):
+        q = copy.deepcopy(p)
+        src = W.gaussian_source(q["source"]["tf_lo"], q["source"]["tf_hi"], (1.0, 9.0))
+        src["t0"] = 2.5 * src["tau"]
+        q["source"] = src
+        out.append(q)
+    return out
+
+
+def test_batched_equals_alone_uneven_grids_and_steps():
+    probs = instances(6, 0)
+    steps = [700, 700, 520, 777, 300, 1100]
+    alone = []
+    for p, n in zip(probs, steps):
+        s = nlfdtd.Solver(p)
+        s.run(n)
+        s.sync()
+        alone.append((fields(s), s.spectra()))
+    batch = [nlfdtd.Solver(p) for p in probs]
+    status = nlfdtd.batch_run(batch, steps)
+    assert status == [0] * len(batch)
+    for s, n, (f_alone, sp_alone) in zip(batch, steps, alone):
+        s.sync()
+        assert s.n == n
+        errs = vec_err(fields(s), f_alone)
+        assert max(errs.values()) <= 1e-5, errs
+        sp = s.spectra()
+        for key in ("ext", "abs", "sca"):
+            ref = sp_alone[key]
+            assert np.max(np.abs(sp[key] - ref)) <= 1e-4 * np.max(np.abs(ref)) + 1e-30, key
+    # every batched instance really went through batched launches
+    assert sum(s.launches for s in batch) > 0
+
+
+def test_batched_instance_matches_oracle():
+    probs = instances(3, 0, nf=8)
+    batch = [nlfdtd.Solver(p) for p in probs]
+    steps = [512, 512, 512]
+    assert nlfdtd.batch_run(batch, steps) == [0, 0, 0]
+    for p, s in zip(probs, batch):
+        s.sync()
+        o = oracle.Sim(p)
+        o.step(512)
+        ref = {c: o.array(c) for comps in VECTORS.values() for c in comps}
+        errs = vec_err(fields(s), ref)
+        assert max(errs.values()) <= 1e-4, errs
+
+
+def test_unstable_instance_is_isolated():
+    """Poison one instance's state with a NaN (through a checkpoint, on the
+    host): it reports NLF_E_UNSTABLE, the others match a batch without it
+    (to rounding: the autotuner may split the work differently)."""
+    probs = instances(3, 0, nf=8)
+    ref = [nlfdtd.Solver(p) for p in probs]
+    assert nlfdtd.batch_run(ref, [512] * 3) == [0, 0, 0]
+    ref_f = [fields(s) for s in ref]
+    runs = [nlfdtd.Solver(p) for p in probs]
+    bad = runs[1]
+    snap = bad.save_state()
+    # the E_x arrays start 256 bytes into the state (after the header): poison one value
+    view = snap.view(np.float32)
+    view[64 + 1000] = np.nan
+    bad.load_state(snap)
+    nlfdtd.batch_run(runs, [512] * 3)
+    with pytest.raises(nlfdtd.NLFError) as ei:
+        bad.sync()
+    assert ei.value.code == -6
+    for q in (0, 2):
+        runs[q].sync()
+        errs = vec_err(fields(runs[q]), ref_f[q])
+        assert max(errs.values()) <= 1e-6, (q, errs)
