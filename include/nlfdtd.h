@@ -244,7 +244,8 @@ int nlf_get_dft(nlf_ctx* ctx, double* dst);
 long long nlf_num_records(const nlf_ctx* ctx);
 
 /* Checkpoint: copy the whole device state (nlf_state_bytes bytes, including
- * the step counter and pending DFT samples) to / from host memory. */
+ * the step counter and pending DFT samples) to / from host memory.  Both
+ * allocate and initialise the state first if no run has done so. */
 int nlf_save_state(nlf_ctx* ctx, void* host);
 int nlf_load_state(nlf_ctx* ctx, const void* host);
 

@@ -1277,7 +1277,8 @@ int nlf_get_dft(nlf_ctx* c, double* dst)
 int nlf_save_state(nlf_ctx* c, void* host)
 {
     if (!c || !host) return NLF_E_ARG;
-    if (!c->ready) return fail(c, NLF_E_STATE, "no state yet");
+    int rc = ensure_ready(c, c->stream);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     Header h{};
     CK(cudaMemcpy(&h, c->base + c->off_hdr, sizeof h, cudaMemcpyDeviceToHost));

@@ -3,12 +3,18 @@
 // One launch advances (H^{n-1/2}, E^n, P^n) to (H^{n+1/2}, E^{n+1}, P^{n+1})
 // in the order of Sec. III: f1 (H), f2 (E), f3 (P_CP), f4 (P_f).  A thread
 // block owns a BX x BY column tile and marches through a chunk of z planes.
-// For plane k it stages E^n of planes k and k+1 (with a one-cell halo) in
-// shared memory, computes H^{n+1/2} of the tile plus the -x / -y halo (the
+// For plane k it stages E^n of planes k and k+1 (tile plus a one-cell halo)
+// in shared memory, computes H^{n+1/2} of the tile plus the -x / -y halo (the
 // halo H is the only recomputed work), keeps H of plane k-1 in registers,
-// and then updates E, P_CP and P_f of the tile.  E, H and psi_H are double
-// buffered (generation n read, n+1 written), so tiles need no grid-wide
-// barrier; every field crosses HBM once per step apart from the halo.
+// and then updates E, P_CP and P_f of the tile.  The loads of plane k+2 and
+// of H^{n-1/2} of plane k+1 are issued into registers before plane k is
+// computed, so their latency overlaps the arithmetic.  E, H and psi_H are
+// double buffered (generation n read, n+1 written), so tiles need no
+// grid-wide barrier; every field crosses HBM once per step apart from halos.
+//
+// Tiles are classified once per block: tiles clear of the CPML slabs, of the
+// TF/SF surface and of the metal box run plain Yee arithmetic with no
+// per-cell tests; the others take the full path.
 //
 // f2/f3/f4 are applied in increment form, algebraically identical to the
 // paper's printed recurrences (Eq. NonlocalUpdate, Eq. GNORUpdate,
@@ -24,13 +30,15 @@
 // (the last line carries the -C4 of substituting f3 into Ampere's law).
 // GD^n = grad(div P_f^n) is evaluated as the difference of node divergences,
 // which equals Eq. GradDiv term by term.
+//
+// Offsets are 32-bit: the library rejects grids with 3 nx ny nz >= 2^32.
 #include <cuda_runtime.h>
 
 #include "nlf_internal.h"
 
 namespace nlf {
 
-__device__ __forceinline__ float ldg(const float* p, long long i) { return __ldg(p + i); }
+constexpr int BX = 32, BY = 8;
 
 // Half-cell offsets of the Yee positions (Table Yee).
 __device__ __forceinline__ int eoff(int c, int a) { return c == a ? 1 : 0; }
@@ -77,26 +85,26 @@ __device__ __forceinline__ int slab_local(const StepParams& p, int a, int v, int
     return -1;
 }
 
-__device__ __forceinline__ long long slab_index(const StepParams& p, int a, int l, int i, int j, int k)
+__device__ __forceinline__ uint32_t slab_index(const StepParams& p, int a, int l, int i, int j, int k)
 {
-    int two = 2 * p.pml;
-    if (a == 0) return ((long long)k * p.ny + j) * two + l;
-    if (a == 1) return ((long long)k * two + l) * p.nx + i;
-    return ((long long)l * p.ny + j) * p.nx + i;
+    const uint32_t two = 2u * (uint32_t)p.pml;
+    if (a == 0) return ((uint32_t)k * p.ny + j) * two + l;
+    if (a == 1) return ((uint32_t)k * two + l) * p.nx + i;
+    return ((uint32_t)l * p.ny + j) * p.nx + i;
 }
 
-// H_C^{n+1/2} at cell (i,j,k) from the E^n values of its curl; if own, also
-// store it and its psi.  (curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2} with
-// (C, A1, A2) cyclic: a_here, a_next = E_{A2} at idx and idx + e_A1,
-// b_here, b_next = E_{A1} at idx and idx + e_A2 (zero beyond the wall).
+// H_C^{n+1/2} at cell (i,j,k), offset q, previous value h0, from the E^n values
+// of its curl, with CPML and TF/SF conversion; if own, store it and its psi.
+// (curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2} with (C, A1, A2) cyclic:
+// a_here, a_next = E_{A2} at idx and idx + e_A1, b_here, b_next = E_{A1} at
+// idx and idx + e_A2 (zero beyond the wall).
 template <int C>
-__device__ __forceinline__ float h_from(const StepParams& p, int i, int j, int k, float a_here, float a_next,
-                                        float b_here, float b_next, bool own)
+__device__ __forceinline__ float h_from(const StepParams& p, int i, int j, int k, uint32_t q, float h0,
+                                        float a_here, float a_next, float b_here, float b_next, bool own)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const int n3[3] = {p.nx, p.ny, p.nz};
     const int ix[3] = {i, j, k};
-    const long long q = ((long long)k * p.ny + j) * p.nx + i;
     if ((A1 == 0 || A2 == 0) && p.tfsf && near_tf(p, i, j, k)) {
         // only E_x carries an incident field; convert it across the TF/SF surface
         const int self = tf_point(p, 2 * i + hoff(C, 0), 2 * j + hoff(C, 1), 2 * k + hoff(C, 2));
@@ -114,82 +122,107 @@ __device__ __forceinline__ float h_from(const StepParams& p, int i, int j, int k
     }
     float t1 = a_next - a_here;
     float t2 = b_next - b_here;
-    int l1 = slab_local(p, A1, ix[A1], n3[A1]);
+    const int l1 = slab_local(p, A1, ix[A1], n3[A1]);
     if (l1 >= 0) {
-        long long s = slab_index(p, A1, l1, i, j, k);
+        const uint32_t s = slab_index(p, A1, l1, i, j, k);
         float psi = __ldg(p.bH[A1] + ix[A1]) * __ldg(p.psiH0[A1][1] + s) + __ldg(p.cH[A1] + ix[A1]) * t1;
         if (own) p.psiH1[A1][1][s] = psi;
         t1 += psi;
     }
-    int l2 = slab_local(p, A2, ix[A2], n3[A2]);
+    const int l2 = slab_local(p, A2, ix[A2], n3[A2]);
     if (l2 >= 0) {
-        long long s = slab_index(p, A2, l2, i, j, k);
+        const uint32_t s = slab_index(p, A2, l2, i, j, k);
         float psi = __ldg(p.bH[A2] + ix[A2]) * __ldg(p.psiH0[A2][0] + s) + __ldg(p.cH[A2] + ix[A2]) * t2;
         if (own) p.psiH1[A2][0][s] = psi;
         t2 += psi;
     }
-    float h = ldg(p.H0[C], q) - p.S * (t1 - t2);
+    const float h = h0 - p.S * (t1 - t2);
     if (own) p.H1[C][q] = h;
     return h;
 }
 
-// Node divergence of P_f^n (difference units) at bbox-local linear index b.
-__device__ __forceinline__ float node_div(const StepParams& p, long long b, long long sy, long long sz)
+// H^{n+1/2} where no CPML, TF/SF surface or metal is near: f1 with nothing else.
+template <int C>
+__device__ __forceinline__ float h_plain(const StepParams& p, uint32_t q, float h0, float a_here, float a_next,
+                                         float b_here, float b_next, bool own)
 {
-    return (ldg(p.P0[0], b) - ldg(p.P0[0], b - 1)) + (ldg(p.P0[1], b) - ldg(p.P0[1], b - sy)) +
-           (ldg(p.P0[2], b) - ldg(p.P0[2], b - sz));
+    const float h = h0 - p.S * ((a_next - a_here) - (b_next - b_here));
+    if (own) p.H1[C][q] = h;
+    return h;
 }
 
-// E_C^{n+1} at cell (i,j,k) from H^{n+1/2}: hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1),
-// hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
-template <int C>
-__device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k, float En, float hA2, float hA2m,
-                                       float hA1, float hA1m, float& d_here, bool& d_valid)
+template <int C, bool BND>
+__device__ __forceinline__ float h_any(const StepParams& p, int i, int j, int k, uint32_t q, float h0, float a0,
+                                       float a1, float b0, float b1, bool own)
+{
+    if (BND) return h_from<C>(p, i, j, k, q, h0, a0, a1, b0, b1, own);
+    return h_plain<C>(p, q, h0, a0, a1, b0, b1, own);
+}
+
+// Node divergence of P_f^n (difference units) at bbox-local offset b.
+__device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint32_t sy, uint32_t sz)
+{
+    return (__ldg(p.P0[0] + b) - __ldg(p.P0[0] + b - 1)) + (__ldg(p.P0[1] + b) - __ldg(p.P0[1] + b - sy)) +
+           (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
+}
+
+// E_C^{n+1} at cell (i,j,k), offset q, from E^n = En and H^{n+1/2}:
+// hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
+// BND: CPML and TF/SF may apply.  The metal update uses the coefficient table mc.
+template <int C, bool BND>
+__device__ __forceinline__ void e_next(const StepParams& p, const MatCoef* mc, int i, int j, int k, uint32_t q,
+                                       float En, float hA2, float hA2m, float hA1, float hA1m, float& d_here,
+                                       bool& d_valid)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const int n3[3] = {p.nx, p.ny, p.nz};
     const int ix[3] = {i, j, k};
-    const long long q = ((long long)k * p.ny + j) * p.nx + i;
-    if ((A1 == 1 || A2 == 1) && p.tfsf && near_tf(p, i, j, k)) {
-        // only H_y carries an incident field
-        const int self = tf_point(p, 2 * i + eoff(C, 0), 2 * j + eoff(C, 1), 2 * k + eoff(C, 2));
-        if (A2 == 1) {   // hA2 = H_y(idx), hA2m = H_y(idx - e_A1)
-            int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
-            int t1 = tf_point(p, 2 * i + 1 - 2 * (A1 == 0), 2 * j - 2 * (A1 == 1), 2 * k + 1 - 2 * (A1 == 2));
-            if (self != t0) hA2 += (self - t0) * h_inc_next(p, k);
-            if (self != t1) hA2m += (self - t1) * h_inc_next(p, k - (A1 == 2));
-        } else {         // hA1 = H_y(idx), hA1m = H_y(idx - e_A2)
-            int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
-            int t1 = tf_point(p, 2 * i + 1 - 2 * (A2 == 0), 2 * j - 2 * (A2 == 1), 2 * k + 1 - 2 * (A2 == 2));
-            if (self != t0) hA1 += (self - t0) * h_inc_next(p, k);
-            if (self != t1) hA1m += (self - t1) * h_inc_next(p, k - (A2 == 2));
+    float t1, t2;
+    if (BND) {
+        if ((A1 == 1 || A2 == 1) && p.tfsf && near_tf(p, i, j, k)) {
+            // only H_y carries an incident field
+            const int self = tf_point(p, 2 * i + eoff(C, 0), 2 * j + eoff(C, 1), 2 * k + eoff(C, 2));
+            if (A2 == 1) {   // hA2 = H_y(idx), hA2m = H_y(idx - e_A1)
+                int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
+                int tt = tf_point(p, 2 * i + 1 - 2 * (A1 == 0), 2 * j - 2 * (A1 == 1), 2 * k + 1 - 2 * (A1 == 2));
+                if (self != t0) hA2 += (self - t0) * h_inc_next(p, k);
+                if (self != tt) hA2m += (self - tt) * h_inc_next(p, k - (A1 == 2));
+            } else {         // hA1 = H_y(idx), hA1m = H_y(idx - e_A2)
+                int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
+                int tt = tf_point(p, 2 * i + 1 - 2 * (A2 == 0), 2 * j - 2 * (A2 == 1), 2 * k + 1 - 2 * (A2 == 2));
+                if (self != t0) hA1 += (self - t0) * h_inc_next(p, k);
+                if (self != tt) hA1m += (self - tt) * h_inc_next(p, k - (A2 == 2));
+            }
         }
-    }
-    float t1 = hA2 - hA2m;
-    float t2 = hA1 - hA1m;
-    int l1 = slab_local(p, A1, ix[A1], n3[A1]);
-    if (l1 >= 0) {
-        long long s = slab_index(p, A1, l1, i, j, k);
-        float psi = __ldg(p.bE[A1] + ix[A1]) * p.psiE[A1][1][s] + __ldg(p.cE[A1] + ix[A1]) * t1;
-        p.psiE[A1][1][s] = psi;
-        t1 += psi;
-    }
-    int l2 = slab_local(p, A2, ix[A2], n3[A2]);
-    if (l2 >= 0) {
-        long long s = slab_index(p, A2, l2, i, j, k);
-        float psi = __ldg(p.bE[A2] + ix[A2]) * p.psiE[A2][0][s] + __ldg(p.cE[A2] + ix[A2]) * t2;
-        p.psiE[A2][0][s] = psi;
-        t2 += psi;
+        t1 = hA2 - hA2m;
+        t2 = hA1 - hA1m;
+        const int l1 = slab_local(p, A1, ix[A1], n3[A1]);
+        if (l1 >= 0) {
+            const uint32_t s = slab_index(p, A1, l1, i, j, k);
+            float psi = __ldg(p.bE[A1] + ix[A1]) * p.psiE[A1][1][s] + __ldg(p.cE[A1] + ix[A1]) * t1;
+            p.psiE[A1][1][s] = psi;
+            t1 += psi;
+        }
+        const int l2 = slab_local(p, A2, ix[A2], n3[A2]);
+        if (l2 >= 0) {
+            const uint32_t s = slab_index(p, A2, l2, i, j, k);
+            float psi = __ldg(p.bE[A2] + ix[A2]) * p.psiE[A2][0][s] + __ldg(p.cE[A2] + ix[A2]) * t2;
+            p.psiE[A2][0][s] = psi;
+            t2 += psi;
+        }
+    } else {
+        t1 = hA2 - hA2m;
+        t2 = hA1 - hA1m;
     }
     const float curl = t1 - t2;
     int id = 0;
-    long long b = 0, sy = 0, sz = 0;
+    uint32_t b = 0, sy = 0, sz = 0;
     if (p.has_metal) {
-        int bi = i - p.bb_lo[0], bj = j - p.bb_lo[1], bk = k - p.bb_lo[2];
+        const int bi = i - p.bb_lo[0], bj = j - p.bb_lo[1], bk = k - p.bb_lo[2];
         if (bi >= 0 && bj >= 0 && bk >= 0 && bi < p.bb_n[0] && bj < p.bb_n[1] && bk < p.bb_n[2]) {
-            sy = p.bb_n[0];
-            sz = (long long)p.bb_n[0] * p.bb_n[1];
-            b = (long long)bk * sz + (long long)bj * sy + bi;
+            sy = (uint32_t)p.bb_n[0];
+            sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
+            b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
             id = p.mat[C][b];
         }
     }
@@ -197,14 +230,14 @@ __device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k,
         p.E1[C][q] = En + p.Sb * curl;
         return;
     }
-    const MatCoef& m = p.coef[id];
+    const MatCoef& m = mc[id];
     float gd = 0.f, af = 0.f;
     if (m.free_e) {
         if (!d_valid) {
             d_here = node_div(p, b, sy, sz);
             d_valid = true;
         }
-        const long long stb = C == 0 ? 1 : (C == 1 ? sy : sz);
+        const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
         gd = node_div(p, b + stb, sy, sz) - d_here;
         af = p.auxf[C][b];
     }
@@ -219,7 +252,7 @@ __device__ __forceinline__ void e_next(const StepParams& p, int i, int j, int k,
     p.E1[C][q] = En + delta;
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
-        p.P1[C][b] = ldg(p.P0[C], b) + dP;
+        p.P1[C][b] = __ldg(p.P0[C] + b) + dP;
         float a_new = -m.D2 * dP + m.D3 * En;
         if (m.gnor) {
             const float g1 = p.gdp[C][b];
@@ -277,134 +310,305 @@ __device__ void inc_step(const StepParams& p, int tid, int nt)
     }
 }
 
-constexpr int BX = 32, BY = 8;
+// ------------------------------------------------------------------ tiles
 
-// Stage E^n of plane kk (tile plus a one-cell halo on every side, zero
-// outside the grid) into shared memory.
-__device__ __forceinline__ void load_plane(const StepParams& p, float (*s)[BY + 2][BX + 2], int x0, int y0, int kk,
-                                           int tid)
+// E^n of one plane held in registers between its load and its store to
+// shared memory: the thread's own cell and (threads 0..NHALO-1) one halo
+// cell: rows y0-1 and y0+BY, columns x0-1 and x0+BX, and the two corners the
+// halo H needs.
+struct PlaneRegs {
+    float in[3];
+    float halo[3];
+};
+
+constexpr int NHALO = 2 * BX + 2 * BY + 2;
+
+__device__ __forceinline__ void halo_cell(int tid, int x0, int y0, int* gi, int* gj, int* sx, int* sy)
 {
-    constexpr int NT = (BY + 2) * (BX + 2);
+    if (tid < BX) {                       // row y0 - 1
+        *gi = x0 + tid; *gj = y0 - 1; *sx = tid + 1; *sy = 0;
+    } else if (tid < 2 * BX) {            // row y0 + BY
+        *gi = x0 + tid - BX; *gj = y0 + BY; *sx = tid - BX + 1; *sy = BY + 1;
+    } else if (tid < 2 * BX + BY) {       // column x0 - 1
+        *gi = x0 - 1; *gj = y0 + tid - 2 * BX; *sx = 0; *sy = tid - 2 * BX + 1;
+    } else if (tid < 2 * BX + 2 * BY) {   // column x0 + BX
+        *gi = x0 + BX; *gj = y0 + tid - 2 * BX - BY; *sx = BX + 1; *sy = tid - 2 * BX - BY + 1;
+    } else if (tid == 2 * BX + 2 * BY) {  // corner (x0 - 1, y0 + BY)
+        *gi = x0 - 1; *gj = y0 + BY; *sx = 0; *sy = BY + 1;
+    } else {                              // corner (x0 + BX, y0 - 1)
+        *gi = x0 + BX; *gj = y0 - 1; *sx = BX + 1; *sy = 0;
+    }
+}
+
+__device__ __forceinline__ void plane_load(const StepParams& p, int x0, int y0, int kk, int tx, int ty, int tid,
+                                           PlaneRegs& r)
+{
     const bool kin = kk >= 0 && kk < p.nz;
-    const long long base = (long long)kk * p.ny * p.nx;
+    const uint32_t base = kin ? (uint32_t)kk * (uint32_t)p.ny * (uint32_t)p.nx : 0u;
+    {
+        const int gi = x0 + tx, gj = y0 + ty;
+        const bool ok = kin && gi < p.nx && gj < p.ny;
+        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.nx + (ok ? gi : 0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float* src = p.E0[c];
-        for (int t = tid; t < NT; t += BX * BY) {
-            const int yy = t / (BX + 2), xx = t - yy * (BX + 2);
-            const int gi = x0 - 1 + xx, gj = y0 - 1 + yy;
-            float v = 0.f;
-            if (kin && gi >= 0 && gi < p.nx && gj >= 0 && gj < p.ny) v = __ldg(src + base + (long long)gj * p.nx + gi);
-            s[c][yy][xx] = v;
+        for (int c = 0; c < 3; ++c) r.in[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
+    }
+    if (tid < NHALO) {
+        int gi, gj, sx, sy;
+        halo_cell(tid, x0, y0, &gi, &gj, &sx, &sy);
+        const bool ok = kin && gi >= 0 && gi < p.nx && gj >= 0 && gj < p.ny;
+        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.nx + (ok ? gi : 0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r.halo[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void plane_store(float (*s)[BY + 2][BX + 2], const PlaneRegs& r, int x0, int y0, int tx,
+                                            int ty, int tid)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c][ty + 1][tx + 1] = r.in[c];
+    if (tid < NHALO) {
+        int gi, gj, sx, sy;
+        halo_cell(tid, x0, y0, &gi, &gj, &sx, &sy);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[c][sy][sx] = r.halo[c];
+    }
+}
+
+// H^{n-1/2} of plane kk at the thread's own cell and, for the halo threads,
+// at its halo H cell (threads 0..BY-1: (x0-1, y0+tid) H_y, H_z;
+// BY..BY+BX-1: (x0+tid-BY, y0-1) H_x, H_z).
+struct HRegs {
+    float own[3];
+    float halo[2];
+};
+
+__device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int kk, int i, int j, bool in, int tid,
+                                       HRegs& r)
+{
+    const uint32_t plane = (uint32_t)p.nx * (uint32_t)p.ny;
+    if (in) {
+        const uint32_t q = (uint32_t)kk * plane + (uint32_t)j * p.nx + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r.own[c] = __ldg(p.H0[c] + q);
+    }
+    if (tid < BY) {
+        const int jh = y0 + tid;
+        if (x0 > 0 && jh < p.ny) {
+            const uint32_t q = (uint32_t)kk * plane + (uint32_t)jh * p.nx + (x0 - 1);
+            r.halo[0] = __ldg(p.H0[1] + q);
+            r.halo[1] = __ldg(p.H0[2] + q);
+        }
+    } else if (tid < BY + BX) {
+        const int ih = x0 + tid - BY;
+        if (y0 > 0 && ih < p.nx) {
+            const uint32_t q = (uint32_t)kk * plane + (uint32_t)(y0 - 1) * p.nx + ih;
+            r.halo[0] = __ldg(p.H0[0] + q);
+            r.halo[1] = __ldg(p.H0[2] + q);
         }
     }
 }
 
-// One tile (bx, by) and z chunk bz of the fused step; every thread of the
-// block must call it (it synchronises the block).  The tile (0,0,0) also
-// advances the 1D incident grid and the step counter.
-__device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, int bz, int kz,
-                                          float (*sE)[3][BY + 2][BX + 2],
-                          float (*sH)[BY + 1][BX + 1])
+// Tile classes (uniform per block): BND = the tile or its halo reaches a CPML
+// slab or the TF surface; MET = it overlaps the metal bounding box.
+template <bool BND, bool MET>
+__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1,
+                                      float (*sE)[3][BY + 2][BX + 2], float (*sH)[BY + 1][BX + 1],
+                                      MatCoef* s_coef)
 {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int x0 = bx * BX, y0 = by * BY;
-    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
-    const int lx = tx + 1, ly = ty + 1;           // position in the staged E tile
+    const int lx = tx + 1, ly = ty + 1;
+    const uint32_t plane = (uint32_t)p.nx * (uint32_t)p.ny;
+    const MatCoef* mc = p.coef;
+    if (MET) {
+        const int nw = (int)((NLF_MAX_MAT + 1) * sizeof(MatCoef) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(p.coef);
+        int* dst = reinterpret_cast<int*>(s_coef);
+        for (int t = tid; t < nw; t += BX * BY) dst[t] = src[t];
+        mc = s_coef;
+    }
     float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
+    PlaneRegs pr;
+    HRegs hr = {{0.f, 0.f, 0.f}, {0.f, 0.f}};
     int cur;
     if (k0 > 0) {
-        load_plane(p, sE[0], x0, y0, k0 - 1, tid);
-        load_plane(p, sE[1], x0, y0, k0, tid);
+        plane_load(p, x0, y0, k0 - 1, tx, ty, tid, pr);
+        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
+        plane_load(p, x0, y0, k0, tx, ty, tid, pr);
+        plane_store(sE[1], pr, x0, y0, tx, ty, tid);
         __syncthreads();
         if (in) {
             const int km = k0 - 1;
-            hx_prev = h_from<0>(p, i, j, km, sE[0][2][ly][lx], sE[0][2][ly + 1][lx], sE[0][1][ly][lx],
-                                sE[1][1][ly][lx], false);
-            hy_prev = h_from<1>(p, i, j, km, sE[0][0][ly][lx], sE[1][0][ly][lx], sE[0][2][ly][lx],
-                                sE[0][2][ly][lx + 1], false);
+            const uint32_t q = (uint32_t)km * plane + (uint32_t)j * p.nx + i;
+            hx_prev = h_any<0, BND>(p, i, j, km, q, __ldg(p.H0[0] + q), sE[0][2][ly][lx], sE[0][2][ly + 1][lx],
+                                    sE[0][1][ly][lx], sE[1][1][ly][lx], false);
+            hy_prev = h_any<1, BND>(p, i, j, km, q, __ldg(p.H0[1] + q), sE[0][0][ly][lx], sE[1][0][ly][lx],
+                                    sE[0][2][ly][lx], sE[0][2][ly][lx + 1], false);
         }
         __syncthreads();
-        load_plane(p, sE[0], x0, y0, k0 + 1, tid);
+        plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
+        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
         cur = 1;
     } else {
-        load_plane(p, sE[0], x0, y0, k0, tid);
-        load_plane(p, sE[1], x0, y0, k0 + 1, tid);
+        plane_load(p, x0, y0, k0, tx, ty, tid, pr);
+        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
+        plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
+        plane_store(sE[1], pr, x0, y0, tx, ty, tid);
         cur = 0;
     }
+    h_load(p, x0, y0, k0, i, j, in, tid, hr);
     __syncthreads();
     for (int k = k0; k < k1; ++k) {
         const int nx_ = cur ^ 1;
+        const bool more = k + 1 < k1;
+        // prefetch plane k+2 of E and plane k+1 of H^{n-1/2}
+        HRegs hn = hr;
+        if (more) {
+            plane_load(p, x0, y0, k + 2, tx, ty, tid, pr);
+            h_load(p, x0, y0, k + 1, i, j, in, tid, hn);
+        }
+        const uint32_t q = (uint32_t)k * plane + (uint32_t)j * p.nx + i;
         float hx = 0.f, hy = 0.f, hz = 0.f;
         // f1: own H^{n+1/2}
         if (in) {
             const float ex = sE[cur][0][ly][lx], ey = sE[cur][1][ly][lx], ez = sE[cur][2][ly][lx];
-            hx = h_from<0>(p, i, j, k, ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
-            hy = h_from<1>(p, i, j, k, ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
-            hz = h_from<2>(p, i, j, k, ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true);
+            hx = h_any<0, BND>(p, i, j, k, q, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
+            hy = h_any<1, BND>(p, i, j, k, q, hr.own[1], ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
+            hz = h_any<2, BND>(p, i, j, k, q, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx],
+                               true);
             sH[0][ly][lx] = hx;
             sH[1][ly][lx] = hy;
             sH[2][ly][lx] = hz;
         }
-        // halo H: H_y, H_z at x0-1 (for E_z, E_y) and H_x, H_z at y0-1 (for E_z, E_x)
-        if (tx == 0 && x0 > 0 && j < p.ny) {
-            const int ih = x0 - 1;
-            sH[1][ly][0] = h_from<1>(p, ih, j, k, sE[cur][0][ly][0], sE[nx_][0][ly][0], sE[cur][2][ly][0],
-                                     sE[cur][2][ly][1], false);
-            sH[2][ly][0] = h_from<2>(p, ih, j, k, sE[cur][1][ly][0], sE[cur][1][ly][1], sE[cur][0][ly][0],
-                                     sE[cur][0][ly + 1][0], false);
-        }
-        if (ty == 0 && y0 > 0 && i < p.nx) {
-            const int jh = y0 - 1;
-            sH[0][0][lx] = h_from<0>(p, i, jh, k, sE[cur][2][0][lx], sE[cur][2][1][lx], sE[cur][1][0][lx],
-                                     sE[nx_][1][0][lx], false);
-            sH[2][0][lx] = h_from<2>(p, i, jh, k, sE[cur][1][0][lx], sE[cur][1][0][lx + 1], sE[cur][0][0][lx],
-                                     sE[cur][0][1][lx], false);
+        // halo H on two warps: H_y, H_z at x0-1 (threads 0..BY-1), H_x, H_z at y0-1 (BY..BY+BX-1)
+        if (tid < BY) {
+            const int jh = y0 + tid, sy = tid + 1;
+            if (x0 > 0 && jh < p.ny) {
+                const int ih = x0 - 1;
+                const uint32_t qh = (uint32_t)k * plane + (uint32_t)jh * p.nx + ih;
+                sH[1][sy][0] = h_any<1, BND>(p, ih, jh, k, qh, hr.halo[0], sE[cur][0][sy][0], sE[nx_][0][sy][0],
+                                             sE[cur][2][sy][0], sE[cur][2][sy][1], false);
+                sH[2][sy][0] = h_any<2, BND>(p, ih, jh, k, qh, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
+                                             sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false);
+            }
+        } else if (tid < BY + BX) {
+            const int ih = x0 + tid - BY, sx = tid - BY + 1;
+            if (y0 > 0 && ih < p.nx) {
+                const int jh = y0 - 1;
+                const uint32_t qh = (uint32_t)k * plane + (uint32_t)jh * p.nx + ih;
+                sH[0][0][sx] = h_any<0, BND>(p, ih, jh, k, qh, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
+                                             sE[cur][1][0][sx], sE[nx_][1][0][sx], false);
+                sH[2][0][sx] = h_any<2, BND>(p, ih, jh, k, qh, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
+                                             sE[cur][0][0][sx], sE[cur][0][1][sx], false);
+            }
         }
         __syncthreads();
         // f2, f3, f4 on the tile
         if (in) {
-            float d_here = 0.f;
-            bool d_valid = false;
-            const long long q = ((long long)k * p.ny + j) * p.nx + i;
-            if (j >= 1 && k >= 1)
-                e_next<0>(p, i, j, k, sE[cur][0][ly][lx], hz, sH[2][ly - 1][lx], hy, hy_prev, d_here, d_valid);
-            else
-                p.E1[0][q] = 0.f;
-            if (i >= 1 && k >= 1)
-                e_next<1>(p, i, j, k, sE[cur][1][ly][lx], hx, hx_prev, hz, sH[2][ly][lx - 1], d_here, d_valid);
-            else
-                p.E1[1][q] = 0.f;
-            if (i >= 1 && j >= 1)
-                e_next<2>(p, i, j, k, sE[cur][2][ly][lx], hy, sH[1][ly][lx - 1], hx, sH[0][ly - 1][lx], d_here,
-                          d_valid);
-            else
-                p.E1[2][q] = 0.f;
+            const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
+            const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
+            if (BND || MET) {
+                float d_here = 0.f;
+                bool d_valid = false;
+                if (j >= 1 && k >= 1)
+                    e_next<0, BND>(p, mc, i, j, k, q, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, d_here, d_valid);
+                else
+                    p.E1[0][q] = 0.f;
+                if (i >= 1 && k >= 1)
+                    e_next<1, BND>(p, mc, i, j, k, q, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, d_here, d_valid);
+                else
+                    p.E1[1][q] = 0.f;
+                if (i >= 1 && j >= 1)
+                    e_next<2, BND>(p, mc, i, j, k, q, sE[cur][2][ly][lx], hy, hyi, hx, hxm, d_here, d_valid);
+                else
+                    p.E1[2][q] = 0.f;
+            } else {
+                // background: eps_b dE = S curl H; tangential E on the walls stays zero
+                p.E1[0][q] = (j >= 1 && k >= 1) ? sE[cur][0][ly][lx] + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
+                p.E1[1][q] = (i >= 1 && k >= 1) ? sE[cur][1][ly][lx] + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
+                p.E1[2][q] = (i >= 1 && j >= 1) ? sE[cur][2][ly][lx] + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
+            }
         }
         hx_prev = hx;
         hy_prev = hy;
+        hr = hn;
         __syncthreads();
-        if (k + 1 < k1) {
-            load_plane(p, sE[cur], x0, y0, k + 2, tid);
+        if (more) {
+            plane_store(sE[cur], pr, x0, y0, tx, ty, tid);
             __syncthreads();
         }
         cur = nx_;
     }
+}
+
+// Does the box [lo, hi] (cells, inclusive) touch a CPML slab, the band of
+// cells next to the TF surface, or the metal box?
+__device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3], const int hi[3], bool* bnd,
+                                           bool* met)
+{
+    const int n3[3] = {p.nx, p.ny, p.nz};
+    bool b = false, m = p.has_metal != 0;
+    bool inner = true, outer = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) b = true;
+        // the per-cell test near_tf() is false for tl < v < th (inner) and for
+        // v < tf_lo - 1 or v > tf_hi (outer)
+        const int tl = p.tf_lo[a], th = a == 1 ? p.tf_hi[a] : p.tf_hi[a] - 1;
+        if (!(lo[a] > tl && hi[a] < th)) inner = false;
+        if (hi[a] < p.tf_lo[a] - 1 || lo[a] > p.tf_hi[a]) outer = true;
+        if (hi[a] < p.bb_lo[a] || lo[a] >= p.bb_lo[a] + p.bb_n[a]) m = false;
+    }
+    if (p.tfsf && !inner && !outer) b = true;
+    *bnd = b;
+    *met = m;
+}
+
+struct TileShared {
+    float sE[2][3][BY + 2][BX + 2];
+    float sH[3][BY + 1][BX + 1];
+    MatCoef coef[NLF_MAX_MAT + 1];
+};
+
+// One tile (bx, by) and z chunk bz of the fused step; every thread of the
+// block must call it (it synchronises the block).  The tile (0,0,0) also
+// advances the 1D incident grid and the step counter.
+__device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, int bz, int kz, TileShared& sm)
+{
+    const int x0 = bx * BX, y0 = by * BY;
+    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
+    const int hi[3] = {x0 + BX, y0 + BY, k1};
+    bool bnd, met;
+    tile_class(p, lo, hi, &bnd, &met);
+    if (bnd) {
+        if (met)
+            march<true, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+        else
+            march<true, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+    } else {
+        if (met)
+            march<false, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+        else
+            march<false, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+    }
     if (bx == 0 && by == 0 && bz == 0) {
+        const int tid = threadIdx.y * BX + threadIdx.x;
         if (p.tfsf) inc_step(p, tid, BX * BY);
         if (tid == 0) *p.step1 = *p.step0 + 1;
-        __syncthreads();
     }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(BX * BY) k_step(const StepParams p, int kz)
 {
-    __shared__ float sE[2][3][BY + 2][BX + 2];
-    __shared__ float sH[3][BY + 1][BX + 1];
-    step_tile(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sE, sH);
+    __shared__ TileShared sm;
+    step_tile(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
 }
+
+// ---------------------------------------------------------------- batched
 
 // Find the instance of work item w: the first q with end[q] > w.
 __device__ __forceinline__ int find_inst(const long long* end, int n, long long w)
@@ -420,10 +624,12 @@ __device__ __forceinline__ int find_inst(const long long* end, int n, long long 
     return lo;
 }
 
+// A persistent grid walks the work items (instance, tile, z chunk) of every
+// instance; each item runs the single-grid tile code with that instance's
+// parameters staged in shared memory.
 __global__ void __launch_bounds__(BX * BY) k_step_batch(const BatchStep a)
 {
-    __shared__ float sE[2][3][BY + 2][BX + 2];
-    __shared__ float sH[3][BY + 1][BX + 1];
+    __shared__ TileShared sm;
     __shared__ StepParams sp;
     __shared__ long long s_end[NLF_MAX_BATCH];
     const int tid = threadIdx.y * BX + threadIdx.x;
@@ -435,7 +641,6 @@ __global__ void __launch_bounds__(BX * BY) k_step_batch(const BatchStep a)
         const int q = find_inst(s_end, a.n, w);
         const BatchInst& I = a.inst[q];
         if (q != loaded) {
-            __syncthreads();
             const int par = I.base_par ^ a.launch_par;
             const int* src = reinterpret_cast<const int*>(&a.params[2 * q + par]);
             int* dst = reinterpret_cast<int*>(&sp);
@@ -449,7 +654,7 @@ __global__ void __launch_bounds__(BX * BY) k_step_batch(const BatchStep a)
         const long long rem = r - bz * per_plane;
         const int by = (int)(rem / I.tiles_x);
         const int bx = (int)(rem - (long long)by * I.tiles_x);
-        step_tile(sp, bx, by, bz, I.kz, sE, sH);
+        step_tile(sp, bx, by, bz, I.kz, sm);
     }
 }
 
