@@ -752,6 +752,7 @@ struct BatchPlan {
     int kz = 0;                       // z chunk used for every instance (0: per-instance heuristic)
     std::vector<int> tried;           // autotuner: candidate z chunks tried so far
     std::vector<float> tried_ms;
+    long long uses = 0;               // segments run with this plan
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     cudaStream_t cap = nullptr;
@@ -855,7 +856,33 @@ int plan_descriptors(BatchPlan* P, int kz)
     return NLF_OK;
 }
 
-// Capture one DFT period of batched launches (step, gathers, flushes).
+// Launch one DFT period of batched work (step, gathers, flushes) on st;
+// returns the number of kernel launches.
+long long plan_launch(BatchPlan* P, cudaStream_t st)
+{
+    long long nodes = 0;
+    int slot = 0;
+    for (int s = 0; s < P->U; ++s) {
+        nlf::BatchStep bs = P->bs;
+        bs.launch_par = s & 1;
+        nlf::launch_step_batch(bs, P->items, st);
+        ++nodes;
+        if (P->mon && (s + 1) % P->K == 0) {
+            nlf::BatchDft bd = P->bd;
+            bd.cur_par = (s + 1) & 1;
+            nlf::launch_gather_batch(bd, P->recs, slot, st);
+            ++nodes;
+            if (++slot == P->B) {
+                nlf::launch_flush_batch(bd, P->phases, P->chunks, P->max_nf, P->B, P->B, st);
+                nodes += 2;
+                slot = 0;
+            }
+        }
+    }
+    return nodes;
+}
+
+// Capture one DFT period of batched launches in a CUDA graph.
 int plan_graph(BatchPlan* P)
 {
     nlf_ctx* c = P->ctxs[0];
@@ -865,26 +892,8 @@ int plan_graph(BatchPlan* P)
     }
     if (!P->cap) CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
-    long long nodes = 0;
     CK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
-    int slot = 0;
-    for (int s = 0; s < P->U; ++s) {
-        nlf::BatchStep bs = P->bs;
-        bs.launch_par = s & 1;
-        nlf::launch_step_batch(bs, P->items, P->cap);
-        ++nodes;
-        if (P->mon && (s + 1) % P->K == 0) {
-            nlf::BatchDft bd = P->bd;
-            bd.cur_par = (s + 1) & 1;
-            nlf::launch_gather_batch(bd, P->recs, slot, P->cap);
-            ++nodes;
-            if (++slot == P->B) {
-                nlf::launch_flush_batch(bd, P->phases, P->chunks, P->max_nf, P->B, P->B, P->cap);
-                nodes += 2;
-                slot = 0;
-            }
-        }
-    }
+    const long long nodes = plan_launch(P, P->cap);
     cudaError_t e = cudaStreamEndCapture(P->cap, &g);
     if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&P->gexec, g, 0);
@@ -898,6 +907,8 @@ double inst_cost(const nlf_ctx* c)
 {
     return (double)c->ncell + 2.0 * (double)c->nbb;   // metal box cells cost about three times a vacuum cell
 }
+
+int g_kz_best = 0;                    // z chunk chosen by the autotuner (0: not tuned yet)
 
 BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
 {
@@ -914,18 +925,18 @@ BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
     P->K = act[0]->K;
     P->B = act[0]->B;
     P->U = act[0]->U;
-    *rcode = plan_descriptors(P.get(), 0);
-    if (*rcode) return nullptr;
-    *rcode = plan_graph(P.get());
+    *rcode = plan_descriptors(P.get(), g_kz_best);
     if (*rcode) return nullptr;
     g_plans.push_back(std::move(P));
     return g_plans.back().get();
 }
 
-// Advance every instance of `act` by one DFT period in batched launches.  The
-// autotuner times the first segments of a plan with each candidate z chunk
-// (every candidate computes the same update; only the work split differs) and
-// keeps the fastest.
+// Advance every instance of `act` by one DFT period in batched launches.
+// Until the autotuner has chosen a z chunk, successive segments run with each
+// candidate (every candidate computes the same update; only the work split
+// differs) timed with events, and the fastest is kept for every later plan.
+// A plan's first segment is launched directly; a plan that comes back is
+// captured once and replayed as a CUDA graph.
 int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -933,34 +944,41 @@ int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
     BatchPlan* P = find_plan(act, &rcode);
     if (!P) return rcode;
     nlf_ctx* c = P->ctxs[0];
-    const bool tuning = P->tried.size() < sizeof(kTuneKz) / sizeof(kTuneKz[0]);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (tuning) {
-        const int kz = kTuneKz[P->tried.size()];
-        if ((rcode = plan_descriptors(P, kz)) || (rcode = plan_graph(P))) return rcode;
+    const int ncand = (int)(sizeof(kTuneKz) / sizeof(kTuneKz[0]));
+    if (g_kz_best == 0) {
+        const int kz = kTuneKz[P->tried.size() % ncand];
+        if ((rcode = plan_descriptors(P, kz))) return rcode;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, st));
-    }
-    CK(cudaGraphLaunch(P->gexec, st));
-    for (nlf_ctx* x : P->ctxs) x->n += P->U;
-    c->launches += P->gnodes;
-    if (tuning) {
+        c->launches += plan_launch(P, st);
+        CK(cudaGetLastError());
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        P->tried.push_back(P->kz);
+        P->tried.push_back(kz);
         P->tried_ms.push_back(ms);
-        if (P->tried.size() == sizeof(kTuneKz) / sizeof(kTuneKz[0])) {
+        if ((int)P->tried.size() == ncand) {
             size_t best = 0;
             for (size_t q = 1; q < P->tried.size(); ++q)
                 if (P->tried_ms[q] < P->tried_ms[best]) best = q;
-            if ((rcode = plan_descriptors(P, P->tried[best])) || (rcode = plan_graph(P))) return rcode;
+            g_kz_best = P->tried[best];
+            if ((rcode = plan_descriptors(P, g_kz_best))) return rcode;
         }
+    } else if (P->uses == 0) {
+        c->launches += plan_launch(P, st);
+        CK(cudaGetLastError());
+    } else {
+        if (!P->gexec && (rcode = plan_graph(P))) return rcode;
+        CK(cudaGraphLaunch(P->gexec, st));
+        c->launches += P->gnodes;
     }
+    P->uses += 1;
+    for (nlf_ctx* x : P->ctxs) x->n += P->U;
     return NLF_OK;
 }
 

@@ -50,17 +50,6 @@ __device__ __forceinline__ bool tf_point(const StepParams& p, int h0, int h1, in
            h2 >= 2 * p.tf_lo[2] && h2 <= 2 * p.tf_hi[2];
 }
 
-// True if cell (i,j,k) or one of its +-1 neighbours lies on the other side
-// of the TF surface, i.e. only for the cells where a TF/SF conversion can apply.
-__device__ __forceinline__ bool near_tf(const StepParams& p, int i, int j, int k)
-{
-    const bool inner = i > p.tf_lo[0] && i < p.tf_hi[0] - 1 && j > p.tf_lo[1] && j < p.tf_hi[1] &&
-                       k > p.tf_lo[2] && k < p.tf_hi[2] - 1;
-    const bool outer = i < p.tf_lo[0] - 1 || i > p.tf_hi[0] || j < p.tf_lo[1] - 1 || j > p.tf_hi[1] ||
-                       k < p.tf_lo[2] - 1 || k > p.tf_hi[2];
-    return !(inner || outer);
-}
-
 __device__ __forceinline__ float e_inc(const StepParams& p, int k)
 {
     int m = k - p.inc_off;
@@ -77,86 +66,94 @@ __device__ __forceinline__ float h_inc_next(const StepParams& p, int k)
 }
 
 // Local index of v inside the CPML slabs of axis a, or -1.
-__device__ __forceinline__ int slab_local(const StepParams& p, int a, int v, int n)
+__device__ __forceinline__ int slab_local(const StepParams& p, int a, int v)
 {
+    const int n = a == 0 ? p.nx : (a == 1 ? p.ny : p.nz);
     if (!p.cpml[a]) return -1;
     if (v < p.pml) return v;
     if (v >= n - p.pml) return v - (n - p.pml) + p.pml;
     return -1;
 }
 
-__device__ __forceinline__ uint32_t slab_index(const StepParams& p, int a, int l, int i, int j, int k)
+// One cell as the update functions see it: its indices, its 32-bit offset and,
+// on CPML tiles, its slab position along each axis (-1: not in that slab) and
+// its offset in that axis' psi arrays.
+struct Cell {
+    int i, j, k;
+    uint32_t q;
+    int l[3];
+    uint32_t s[3];
+};
+
+__device__ __forceinline__ void cell_slabs(const StepParams& p, Cell& c)
 {
     const uint32_t two = 2u * (uint32_t)p.pml;
-    if (a == 0) return ((uint32_t)k * p.ny + j) * two + l;
-    if (a == 1) return ((uint32_t)k * two + l) * p.nx + i;
-    return ((uint32_t)l * p.ny + j) * p.nx + i;
+    c.s[0] = c.l[0] >= 0 ? ((uint32_t)c.k * p.ny + c.j) * two + c.l[0] : 0u;
+    c.s[1] = c.l[1] >= 0 ? ((uint32_t)c.k * two + c.l[1]) * p.nx + c.i : 0u;
+    c.s[2] = c.l[2] >= 0 ? ((uint32_t)c.l[2] * p.ny + c.j) * p.nx + c.i : 0u;
 }
 
-// H_C^{n+1/2} at cell (i,j,k), offset q, previous value h0, from the E^n values
-// of its curl, with CPML and TF/SF conversion; if own, store it and its psi.
-// (curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2} with (C, A1, A2) cyclic:
-// a_here, a_next = E_{A2} at idx and idx + e_A1, b_here, b_next = E_{A1} at
-// idx and idx + e_A2 (zero beyond the wall).
-template <int C>
-__device__ __forceinline__ float h_from(const StepParams& p, int i, int j, int k, uint32_t q, float h0,
-                                        float a_here, float a_next, float b_here, float b_next, bool own)
+__device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int k, bool pml)
+{
+    Cell c;
+    c.i = i;
+    c.j = j;
+    c.k = k;
+    c.q = ((uint32_t)k * p.ny + j) * p.nx + i;
+    c.l[0] = c.l[1] = c.l[2] = -1;
+    if (pml) {
+        c.l[0] = slab_local(p, 0, i);
+        c.l[1] = slab_local(p, 1, j);
+        c.l[2] = slab_local(p, 2, k);
+        cell_slabs(p, c);
+    }
+    return c;
+}
+
+// H_C^{n+1/2} at cell c from H^{n-1/2} = h0 and the E^n values of its curl
+// ((curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2}, (C, A1, A2) cyclic):
+// a_here, a_next = E_{A2} at idx and idx + e_A1, b_here, b_next = E_{A1} at idx
+// and idx + e_A2 (zero beyond the wall).  If own, store it and its psi.
+//
+// TF: the incident plane wave (E_x, H_y along +z) is converted where an H
+// read crosses the TF surface: H_y on the planes k = lo_z - 1 and k = hi_z
+// and H_z on the planes j = lo_y - 1 and j = hi_y are scattered fields whose
+// E_x neighbour on the other side is a total field.
+template <int C, bool PML, bool TF>
+__device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, float h0, float a_here, float a_next,
+                                        float b_here, float b_next, bool own)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    const int n3[3] = {p.nx, p.ny, p.nz};
-    const int ix[3] = {i, j, k};
-    if ((A1 == 0 || A2 == 0) && p.tfsf && near_tf(p, i, j, k)) {
-        // only E_x carries an incident field; convert it across the TF/SF surface
-        const int self = tf_point(p, 2 * i + hoff(C, 0), 2 * j + hoff(C, 1), 2 * k + hoff(C, 2));
-        if (A2 == 0) {   // a_* are E_x at idx and idx + e_A1
-            int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k);
-            int t1 = tf_point(p, 2 * i + 1 + 2 * (A1 == 0), 2 * j + 2 * (A1 == 1), 2 * k + 2 * (A1 == 2));
-            if (self != t0) a_here += (self - t0) * e_inc(p, k);
-            if (self != t1) a_next += (self - t1) * e_inc(p, k + (A1 == 2));
-        } else {         // b_* are E_x at idx and idx + e_A2
-            int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k);
-            int t1 = tf_point(p, 2 * i + 1 + 2 * (A2 == 0), 2 * j + 2 * (A2 == 1), 2 * k + 2 * (A2 == 2));
-            if (self != t0) b_here += (self - t0) * e_inc(p, k);
-            if (self != t1) b_next += (self - t1) * e_inc(p, k + (A2 == 2));
+    if (TF) {
+        if (C == 1 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1]) {
+            if (c.k == p.tf_lo[2] - 1) a_next -= e_inc(p, p.tf_lo[2]);
+            if (c.k == p.tf_hi[2]) a_here -= e_inc(p, p.tf_hi[2]);
+        }
+        if (C == 2 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.k >= p.tf_lo[2] && c.k <= p.tf_hi[2]) {
+            if (c.j == p.tf_lo[1] - 1) b_next -= e_inc(p, c.k);
+            if (c.j == p.tf_hi[1]) b_here -= e_inc(p, c.k);
         }
     }
     float t1 = a_next - a_here;
     float t2 = b_next - b_here;
-    const int l1 = slab_local(p, A1, ix[A1], n3[A1]);
-    if (l1 >= 0) {
-        const uint32_t s = slab_index(p, A1, l1, i, j, k);
-        float psi = __ldg(p.bH[A1] + ix[A1]) * __ldg(p.psiH0[A1][1] + s) + __ldg(p.cH[A1] + ix[A1]) * t1;
-        if (own) p.psiH1[A1][1][s] = psi;
-        t1 += psi;
-    }
-    const int l2 = slab_local(p, A2, ix[A2], n3[A2]);
-    if (l2 >= 0) {
-        const uint32_t s = slab_index(p, A2, l2, i, j, k);
-        float psi = __ldg(p.bH[A2] + ix[A2]) * __ldg(p.psiH0[A2][0] + s) + __ldg(p.cH[A2] + ix[A2]) * t2;
-        if (own) p.psiH1[A2][0][s] = psi;
-        t2 += psi;
+    if (PML) {
+        const int ix[3] = {c.i, c.j, c.k};
+        if (c.l[A1] >= 0) {
+            const float psi = __ldg(p.bH[A1] + ix[A1]) * __ldg(p.psiH0[A1][1] + c.s[A1]) +
+                              __ldg(p.cH[A1] + ix[A1]) * t1;
+            if (own) p.psiH1[A1][1][c.s[A1]] = psi;
+            t1 += psi;
+        }
+        if (c.l[A2] >= 0) {
+            const float psi = __ldg(p.bH[A2] + ix[A2]) * __ldg(p.psiH0[A2][0] + c.s[A2]) +
+                              __ldg(p.cH[A2] + ix[A2]) * t2;
+            if (own) p.psiH1[A2][0][c.s[A2]] = psi;
+            t2 += psi;
+        }
     }
     const float h = h0 - p.S * (t1 - t2);
-    if (own) p.H1[C][q] = h;
+    if (own) p.H1[C][c.q] = h;
     return h;
-}
-
-// H^{n+1/2} where no CPML, TF/SF surface or metal is near: f1 with nothing else.
-template <int C>
-__device__ __forceinline__ float h_plain(const StepParams& p, uint32_t q, float h0, float a_here, float a_next,
-                                         float b_here, float b_next, bool own)
-{
-    const float h = h0 - p.S * ((a_next - a_here) - (b_next - b_here));
-    if (own) p.H1[C][q] = h;
-    return h;
-}
-
-template <int C, bool BND>
-__device__ __forceinline__ float h_any(const StepParams& p, int i, int j, int k, uint32_t q, float h0, float a0,
-                                       float a1, float b0, float b1, bool own)
-{
-    if (BND) return h_from<C>(p, i, j, k, q, h0, a0, a1, b0, b1, own);
-    return h_plain<C>(p, q, h0, a0, a1, b0, b1, own);
 }
 
 // Node divergence of P_f^n (difference units) at bbox-local offset b.
@@ -166,59 +163,46 @@ __device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint3
            (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
 }
 
-// E_C^{n+1} at cell (i,j,k), offset q, from E^n = En and H^{n+1/2}:
-// hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
-// BND: CPML and TF/SF may apply.  The metal update uses the coefficient table mc.
-template <int C, bool BND>
-__device__ __forceinline__ void e_next(const StepParams& p, const MatCoef* mc, int i, int j, int k, uint32_t q,
-                                       float En, float hA2, float hA2m, float hA1, float hA1m, float& d_here,
-                                       bool& d_valid)
+// E_C^{n+1} at cell c from E^n = En and H^{n+1/2}: hA2 = H_{A2}(idx),
+// hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
+// TF: E_x on the planes k = lo_z and k = hi_z, and E_z on the planes
+// i = lo_x and i = hi_x, are total fields reading a scattered H_y.
+// MET: the site may hold a material (coefficient table mc).
+template <int C, bool PML, bool TF, bool MET>
+__device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, const Cell& c, float En, float hA2,
+                                       float hA2m, float hA1, float hA1m, float& d_here, bool& d_valid)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    const int n3[3] = {p.nx, p.ny, p.nz};
-    const int ix[3] = {i, j, k};
-    float t1, t2;
-    if (BND) {
-        if ((A1 == 1 || A2 == 1) && p.tfsf && near_tf(p, i, j, k)) {
-            // only H_y carries an incident field
-            const int self = tf_point(p, 2 * i + eoff(C, 0), 2 * j + eoff(C, 1), 2 * k + eoff(C, 2));
-            if (A2 == 1) {   // hA2 = H_y(idx), hA2m = H_y(idx - e_A1)
-                int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
-                int tt = tf_point(p, 2 * i + 1 - 2 * (A1 == 0), 2 * j - 2 * (A1 == 1), 2 * k + 1 - 2 * (A1 == 2));
-                if (self != t0) hA2 += (self - t0) * h_inc_next(p, k);
-                if (self != tt) hA2m += (self - tt) * h_inc_next(p, k - (A1 == 2));
-            } else {         // hA1 = H_y(idx), hA1m = H_y(idx - e_A2)
-                int t0 = tf_point(p, 2 * i + 1, 2 * j, 2 * k + 1);
-                int tt = tf_point(p, 2 * i + 1 - 2 * (A2 == 0), 2 * j - 2 * (A2 == 1), 2 * k + 1 - 2 * (A2 == 2));
-                if (self != t0) hA1 += (self - t0) * h_inc_next(p, k);
-                if (self != tt) hA1m += (self - tt) * h_inc_next(p, k - (A2 == 2));
-            }
+    if (TF) {
+        if (C == 0 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1]) {
+            if (c.k == p.tf_lo[2]) hA1m += h_inc_next(p, p.tf_lo[2] - 1);
+            if (c.k == p.tf_hi[2]) hA1 += h_inc_next(p, p.tf_hi[2]);
         }
-        t1 = hA2 - hA2m;
-        t2 = hA1 - hA1m;
-        const int l1 = slab_local(p, A1, ix[A1], n3[A1]);
-        if (l1 >= 0) {
-            const uint32_t s = slab_index(p, A1, l1, i, j, k);
-            float psi = __ldg(p.bE[A1] + ix[A1]) * p.psiE[A1][1][s] + __ldg(p.cE[A1] + ix[A1]) * t1;
-            p.psiE[A1][1][s] = psi;
+        if (C == 2 && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1] && c.k >= p.tf_lo[2] && c.k < p.tf_hi[2]) {
+            if (c.i == p.tf_lo[0]) hA2m += h_inc_next(p, c.k);
+            if (c.i == p.tf_hi[0]) hA2 += h_inc_next(p, c.k);
+        }
+    }
+    float t1 = hA2 - hA2m;
+    float t2 = hA1 - hA1m;
+    if (PML) {
+        const int ix[3] = {c.i, c.j, c.k};
+        if (c.l[A1] >= 0) {
+            const float psi = __ldg(p.bE[A1] + ix[A1]) * p.psiE[A1][1][c.s[A1]] + __ldg(p.cE[A1] + ix[A1]) * t1;
+            p.psiE[A1][1][c.s[A1]] = psi;
             t1 += psi;
         }
-        const int l2 = slab_local(p, A2, ix[A2], n3[A2]);
-        if (l2 >= 0) {
-            const uint32_t s = slab_index(p, A2, l2, i, j, k);
-            float psi = __ldg(p.bE[A2] + ix[A2]) * p.psiE[A2][0][s] + __ldg(p.cE[A2] + ix[A2]) * t2;
-            p.psiE[A2][0][s] = psi;
+        if (c.l[A2] >= 0) {
+            const float psi = __ldg(p.bE[A2] + ix[A2]) * p.psiE[A2][0][c.s[A2]] + __ldg(p.cE[A2] + ix[A2]) * t2;
+            p.psiE[A2][0][c.s[A2]] = psi;
             t2 += psi;
         }
-    } else {
-        t1 = hA2 - hA2m;
-        t2 = hA1 - hA1m;
     }
     const float curl = t1 - t2;
     int id = 0;
     uint32_t b = 0, sy = 0, sz = 0;
-    if (p.has_metal) {
-        const int bi = i - p.bb_lo[0], bj = j - p.bb_lo[1], bk = k - p.bb_lo[2];
+    if (MET) {
+        const int bi = c.i - p.bb_lo[0], bj = c.j - p.bb_lo[1], bk = c.k - p.bb_lo[2];
         if (bi >= 0 && bj >= 0 && bk >= 0 && bi < p.bb_n[0] && bj < p.bb_n[1] && bk < p.bb_n[2]) {
             sy = (uint32_t)p.bb_n[0];
             sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
@@ -227,7 +211,7 @@ __device__ __forceinline__ void e_next(const StepParams& p, const MatCoef* mc, i
         }
     }
     if (id == 0) {
-        p.E1[C][q] = En + p.Sb * curl;
+        p.E1[C][c.q] = En + p.Sb * curl;
         return;
     }
     const MatCoef& m = mc[id];
@@ -249,7 +233,7 @@ __device__ __forceinline__ void e_next(const StepParams& p, const MatCoef* mc, i
         acs += ac[pp];
     }
     const float delta = (p.S * curl - af - acs - m.G * gd - m.cE * En) * m.inv_den;
-    p.E1[C][q] = En + delta;
+    p.E1[C][c.q] = En + delta;
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
         p.P1[C][b] = __ldg(p.P0[C] + b) + dP;
@@ -409,9 +393,11 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
     }
 }
 
-// Tile classes (uniform per block): BND = the tile or its halo reaches a CPML
-// slab or the TF surface; MET = it overlaps the metal bounding box.
-template <bool BND, bool MET>
+// Tile classes (uniform per block): PML = the tile or its halo reaches a
+// CPML slab; TF = it reaches the cells next to the TF/SF surface; MET = it
+// overlaps the metal bounding box.  A tile of none of the classes runs plain
+// Yee arithmetic with no per-cell test.
+template <bool PML, bool TF, bool MET>
 __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1,
                                       float (*sE)[3][BY + 2][BX + 2], float (*sH)[BY + 1][BX + 1],
                                       MatCoef* s_coef)
@@ -420,7 +406,6 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
     const int lx = tx + 1, ly = ty + 1;
-    const uint32_t plane = (uint32_t)p.nx * (uint32_t)p.ny;
     const MatCoef* mc = p.coef;
     if (MET) {
         const int nw = (int)((NLF_MAX_MAT + 1) * sizeof(MatCoef) / sizeof(int));
@@ -429,6 +414,8 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         for (int t = tid; t < nw; t += BX * BY) dst[t] = src[t];
         mc = s_coef;
     }
+    // slab positions of the own column and of the halo cells (constant along z)
+    const int slx = PML ? slab_local(p, 0, i) : -1, sly = PML ? slab_local(p, 1, j) : -1;
     float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
     PlaneRegs pr;
     HRegs hr = {{0.f, 0.f, 0.f}, {0.f, 0.f}};
@@ -440,12 +427,11 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         plane_store(sE[1], pr, x0, y0, tx, ty, tid);
         __syncthreads();
         if (in) {
-            const int km = k0 - 1;
-            const uint32_t q = (uint32_t)km * plane + (uint32_t)j * p.nx + i;
-            hx_prev = h_any<0, BND>(p, i, j, km, q, __ldg(p.H0[0] + q), sE[0][2][ly][lx], sE[0][2][ly + 1][lx],
-                                    sE[0][1][ly][lx], sE[1][1][ly][lx], false);
-            hy_prev = h_any<1, BND>(p, i, j, km, q, __ldg(p.H0[1] + q), sE[0][0][ly][lx], sE[1][0][ly][lx],
-                                    sE[0][2][ly][lx], sE[0][2][ly][lx + 1], false);
+            const Cell c = make_cell(p, i, j, k0 - 1, PML);
+            hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), sE[0][2][ly][lx], sE[0][2][ly + 1][lx],
+                                         sE[0][1][ly][lx], sE[1][1][ly][lx], false);
+            hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), sE[0][0][ly][lx], sE[1][0][ly][lx],
+                                         sE[0][2][ly][lx], sE[0][2][ly][lx + 1], false);
         }
         __syncthreads();
         plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
@@ -469,15 +455,22 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             plane_load(p, x0, y0, k + 2, tx, ty, tid, pr);
             h_load(p, x0, y0, k + 1, i, j, in, tid, hn);
         }
-        const uint32_t q = (uint32_t)k * plane + (uint32_t)j * p.nx + i;
+        Cell c;
+        c.i = i;
+        c.j = j;
+        c.k = k;
+        c.q = ((uint32_t)k * p.ny + j) * p.nx + i;
+        c.l[0] = slx;
+        c.l[1] = sly;
+        c.l[2] = PML ? slab_local(p, 2, k) : -1;
+        if (PML) cell_slabs(p, c);
         float hx = 0.f, hy = 0.f, hz = 0.f;
         // f1: own H^{n+1/2}
         if (in) {
             const float ex = sE[cur][0][ly][lx], ey = sE[cur][1][ly][lx], ez = sE[cur][2][ly][lx];
-            hx = h_any<0, BND>(p, i, j, k, q, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
-            hy = h_any<1, BND>(p, i, j, k, q, hr.own[1], ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
-            hz = h_any<2, BND>(p, i, j, k, q, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx],
-                               true);
+            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
+            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
+            hz = h_cell<2, PML, TF>(p, c, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true);
             sH[0][ly][lx] = hx;
             sH[1][ly][lx] = hy;
             sH[2][ly][lx] = hz;
@@ -486,49 +479,47 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         if (tid < BY) {
             const int jh = y0 + tid, sy = tid + 1;
             if (x0 > 0 && jh < p.ny) {
-                const int ih = x0 - 1;
-                const uint32_t qh = (uint32_t)k * plane + (uint32_t)jh * p.nx + ih;
-                sH[1][sy][0] = h_any<1, BND>(p, ih, jh, k, qh, hr.halo[0], sE[cur][0][sy][0], sE[nx_][0][sy][0],
-                                             sE[cur][2][sy][0], sE[cur][2][sy][1], false);
-                sH[2][sy][0] = h_any<2, BND>(p, ih, jh, k, qh, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
-                                             sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false);
+                const Cell h = make_cell(p, x0 - 1, jh, k, PML);
+                sH[1][sy][0] = h_cell<1, PML, TF>(p, h, hr.halo[0], sE[cur][0][sy][0], sE[nx_][0][sy][0],
+                                                  sE[cur][2][sy][0], sE[cur][2][sy][1], false);
+                sH[2][sy][0] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
+                                                  sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false);
             }
         } else if (tid < BY + BX) {
             const int ih = x0 + tid - BY, sx = tid - BY + 1;
             if (y0 > 0 && ih < p.nx) {
-                const int jh = y0 - 1;
-                const uint32_t qh = (uint32_t)k * plane + (uint32_t)jh * p.nx + ih;
-                sH[0][0][sx] = h_any<0, BND>(p, ih, jh, k, qh, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
-                                             sE[cur][1][0][sx], sE[nx_][1][0][sx], false);
-                sH[2][0][sx] = h_any<2, BND>(p, ih, jh, k, qh, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
-                                             sE[cur][0][0][sx], sE[cur][0][1][sx], false);
+                const Cell h = make_cell(p, ih, y0 - 1, k, PML);
+                sH[0][0][sx] = h_cell<0, PML, TF>(p, h, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
+                                                  sE[cur][1][0][sx], sE[nx_][1][0][sx], false);
+                sH[2][0][sx] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
+                                                  sE[cur][0][0][sx], sE[cur][0][1][sx], false);
             }
         }
         __syncthreads();
-        // f2, f3, f4 on the tile
+        // f2, f3, f4 on the tile; tangential E on the walls stays zero
         if (in) {
             const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
             const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
-            if (BND || MET) {
+            if (PML || TF || MET) {
                 float d_here = 0.f;
                 bool d_valid = false;
                 if (j >= 1 && k >= 1)
-                    e_next<0, BND>(p, mc, i, j, k, q, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, d_here, d_valid);
+                    e_cell<0, PML, TF, MET>(p, mc, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, d_here, d_valid);
                 else
-                    p.E1[0][q] = 0.f;
+                    p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_next<1, BND>(p, mc, i, j, k, q, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, d_here, d_valid);
+                    e_cell<1, PML, TF, MET>(p, mc, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, d_here, d_valid);
                 else
-                    p.E1[1][q] = 0.f;
+                    p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_next<2, BND>(p, mc, i, j, k, q, sE[cur][2][ly][lx], hy, hyi, hx, hxm, d_here, d_valid);
+                    e_cell<2, PML, TF, MET>(p, mc, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm, d_here, d_valid);
                 else
-                    p.E1[2][q] = 0.f;
+                    p.E1[2][c.q] = 0.f;
             } else {
-                // background: eps_b dE = S curl H; tangential E on the walls stays zero
-                p.E1[0][q] = (j >= 1 && k >= 1) ? sE[cur][0][ly][lx] + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
-                p.E1[1][q] = (i >= 1 && k >= 1) ? sE[cur][1][ly][lx] + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
-                p.E1[2][q] = (i >= 1 && j >= 1) ? sE[cur][2][ly][lx] + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
+                // background: eps_b dE = S curl H
+                p.E1[0][c.q] = (j >= 1 && k >= 1) ? sE[cur][0][ly][lx] + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
+                p.E1[1][c.q] = (i >= 1 && k >= 1) ? sE[cur][1][ly][lx] + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
+                p.E1[2][c.q] = (i >= 1 && j >= 1) ? sE[cur][2][ly][lx] + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
             }
         }
         hx_prev = hx;
@@ -543,10 +534,11 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     }
 }
 
-// Does the box [lo, hi] (cells, inclusive) touch a CPML slab, the band of
-// cells next to the TF surface, or the metal box?
-__device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3], const int hi[3], bool* bnd,
-                                           bool* met)
+// Classes of the box [lo, hi] (cells, inclusive): does it touch a CPML slab,
+// a cell on which a TF/SF conversion happens (within one cell of the TF
+// surface), or the metal box?
+__device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3], const int hi[3], bool* pml,
+                                           bool* tf, bool* met)
 {
     const int n3[3] = {p.nx, p.ny, p.nz};
     bool b = false, m = p.has_metal != 0;
@@ -554,15 +546,13 @@ __device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3],
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) b = true;
-        // the per-cell test near_tf() is false for tl < v < th (inner) and for
-        // v < tf_lo - 1 or v > tf_hi (outer)
-        const int tl = p.tf_lo[a], th = a == 1 ? p.tf_hi[a] : p.tf_hi[a] - 1;
-        if (!(lo[a] > tl && hi[a] < th)) inner = false;
+        // every conversion sits on the planes tf_lo - 1 .. tf_lo or tf_hi .. (tf_hi) of some axis
+        if (!(lo[a] > p.tf_lo[a] && hi[a] < p.tf_hi[a] - 1)) inner = false;
         if (hi[a] < p.tf_lo[a] - 1 || lo[a] > p.tf_hi[a]) outer = true;
         if (hi[a] < p.bb_lo[a] || lo[a] >= p.bb_lo[a] + p.bb_n[a]) m = false;
     }
-    if (p.tfsf && !inner && !outer) b = true;
-    *bnd = b;
+    *pml = b;
+    *tf = p.tfsf && !inner && !outer;
     *met = m;
 }
 
@@ -571,6 +561,15 @@ struct TileShared {
     float sH[3][BY + 1][BX + 1];
     MatCoef coef[NLF_MAX_MAT + 1];
 };
+
+template <bool PML, bool TF>
+__device__ __forceinline__ void march_m(const StepParams& p, bool met, int x0, int y0, int k0, int k1, TileShared& sm)
+{
+    if (met)
+        march<PML, TF, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+    else
+        march<PML, TF, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+}
 
 // One tile (bx, by) and z chunk bz of the fused step; every thread of the
 // block must call it (it synchronises the block).  The tile (0,0,0) also
@@ -581,18 +580,18 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, i
     const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
-    bool bnd, met;
-    tile_class(p, lo, hi, &bnd, &met);
-    if (bnd) {
-        if (met)
-            march<true, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+    bool pml, tf, met;
+    tile_class(p, lo, hi, &pml, &tf, &met);
+    if (pml) {
+        if (tf)
+            march_m<true, true>(p, met, x0, y0, k0, k1, sm);
         else
-            march<true, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+            march_m<true, false>(p, met, x0, y0, k0, k1, sm);
     } else {
-        if (met)
-            march<false, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+        if (tf)
+            march_m<false, true>(p, met, x0, y0, k0, k1, sm);
         else
-            march<false, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+            march_m<false, false>(p, met, x0, y0, k0, k1, sm);
     }
     if (bx == 0 && by == 0 && bz == 0) {
         const int tid = threadIdx.y * BX + threadIdx.x;
@@ -602,7 +601,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, i
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(BX * BY) k_step(const StepParams p, int kz)
+__global__ void __launch_bounds__(BX * BY, 4) k_step(const StepParams p, int kz)
 {
     __shared__ TileShared sm;
     step_tile(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
@@ -627,7 +626,7 @@ __device__ __forceinline__ int find_inst(const long long* end, int n, long long 
 // A persistent grid walks the work items (instance, tile, z chunk) of every
 // instance; each item runs the single-grid tile code with that instance's
 // parameters staged in shared memory.
-__global__ void __launch_bounds__(BX * BY) k_step_batch(const BatchStep a)
+__global__ void __launch_bounds__(BX * BY, 4) k_step_batch(const BatchStep a)
 {
     __shared__ TileShared sm;
     __shared__ StepParams sp;
