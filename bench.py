@@ -18,6 +18,8 @@ explicit L2 flush is needed between steps.
            CUDA-event duration (single-step launches at the end of each solve)
            against the measured HBM copy bandwidth
   cpu_baseline - the FP64 CPU oracle on a bounded sample of the same workload
+  serving - solves/s and p50/p99 latency of the seeded request stream's first
+           requests, continuous batching against one grid at a time
 
 `--impl reference` times the oracle alone (the reference arm).  With several
 GPUs (torchrun) every rank runs its own independent replica ("replicas only":
@@ -242,6 +244,10 @@ def run_ours(args, rank, world, dist):
     e2e_val = steps * cells / statistics.mean(e2e_times) / 1e9 * world
     del solver
 
+    serving = None
+    if args.serving > 0:
+        serving = run_serving(args.serving)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sample = prob["monitors"]["K"]
@@ -278,7 +284,26 @@ def run_ours(args, rank, world, dist):
             "cpu_baseline": cpu,
             "spectrum_peak_ev": float(prob["monitors"]["omega"][int(spec["ext"].argmax())] / W.EV_TO_RAD),
         }
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
+
+
+def run_serving(n):
+    """The first n requests of the seeded Poisson stream (20 req/s; sphere /
+    dimer / cube-with-tips solves on 48^3..320^3 grids, 2000..8000 steps, GNOR
+    on or off) served by continuous batching with HBM-budget admission, and by
+    the plain one-grid-at-a-time FIFO form."""
+    from paper_2005_06997_gb300 import serve
+    from paper_2005_06997_gb300 import workloads as W
+    reqs = W.serving_requests()[:n]
+    out = {"requests": n, "rate_req_per_s": 20.0, "hbm_budget_gb": 200}
+    _, sb = serve.Server(hbm_budget_bytes=200 << 30).run(reqs)
+    _, sf = serve.serve_fifo(reqs)
+    keys = ("solves_per_s", "p50_latency_s", "p99_latency_s", "gcell_updates_per_s", "wall_s")
+    out["batched"] = {k: sb[k] for k in keys}
+    out["fifo"] = {k: sf[k] for k in keys}
+    return out
 
 
 def info_bytes(prob):
@@ -305,6 +330,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=48, help="requests of the serving stream to run (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -156,21 +156,25 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
     return h;
 }
 
-// Node divergence of P_f^n (difference units) at bbox-local offset b.
-__device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint32_t sy, uint32_t sz)
+// P_f^n component c at cell (x, y, kk); zero outside the metal box (P_f is
+// zero off the metal, Pekar, and the box carries a two-cell margin).
+__device__ __forceinline__ float p_at(const StepParams& p, int c, int x, int y, int kk)
 {
-    return (__ldg(p.P0[0] + b) - __ldg(p.P0[0] + b - 1)) + (__ldg(p.P0[1] + b) - __ldg(p.P0[1] + b - sy)) +
-           (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
+    const int bi = x - p.bb_lo[0], bj = y - p.bb_lo[1], bk = kk - p.bb_lo[2];
+    if (bi < 0 || bj < 0 || bk < 0 || bi >= p.bb_n[0] || bj >= p.bb_n[1] || bk >= p.bb_n[2]) return 0.f;
+    const uint32_t b = ((uint32_t)bk * p.bb_n[1] + bj) * p.bb_n[0] + bi;
+    return __ldg(p.P0[c] + b);
 }
 
 // E_C^{n+1} at cell c from E^n = En and H^{n+1/2}: hA2 = H_{A2}(idx),
-// hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
+// hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2);
+// gd_c = (grad div P_f^n)_C at the site (metal tiles).
 // TF: E_x on the planes k = lo_z and k = hi_z, and E_z on the planes
 // i = lo_x and i = hi_x, are total fields reading a scattered H_y.
 // MET: the site may hold a material (coefficient table mc).
 template <int C, bool PML, bool TF, bool MET>
 __device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, const Cell& c, float En, float hA2,
-                                       float hA2m, float hA1, float hA1m, float& d_here, bool& d_valid)
+                                       float hA2m, float hA1, float hA1m, float gd_c)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     if (TF) {
@@ -217,12 +221,7 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, c
     const MatCoef& m = mc[id];
     float gd = 0.f, af = 0.f;
     if (m.free_e) {
-        if (!d_valid) {
-            d_here = node_div(p, b, sy, sz);
-            d_valid = true;
-        }
-        const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
-        gd = node_div(p, b + stb, sy, sz) - d_here;
+        gd = gd_c;
         af = p.auxf[C][b];
     }
     float ac[NLF_MAX_POLES];
@@ -393,15 +392,51 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
     }
 }
 
+struct TileShared {
+    float sE[2][3][BY + 2][BX + 2];
+    float sH[3][BY + 1][BX + 1];
+    MatCoef coef[NLF_MAX_MAT + 1];
+    // metal tiles: P_x, P_y of one plane at x0-1..x0+BX, y0-1..y0+BY; P_z and
+    // the node divergence of two planes (by parity) at x0..x0+BX, y0..y0+BY
+    float Pxy[2][BY + 2][BX + 2];
+    float Pz[2][BY + 1][BX + 1];
+    float D[2][BY + 1][BX + 1];
+};
+
+// Node divergence of P_f^n (difference units) for plane kk into slot kk & 1:
+// d(x, y) = P_x(x) - P_x(x-1) + P_y(y) - P_y(y-1) + P_z(kk) - P_z(kk-1) at the
+// nodes x0..x0+BX, y0..y0+BY (P_z(kk-1) is the other slot, staged before).
+__device__ __forceinline__ void div_plane(const StepParams& p, TileShared& sm, int x0, int y0, int kk, int tid)
+{
+    const int s = kk & 1;
+    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
+        const int a = t / (BX + 2), b = t - a * (BX + 2);
+        sm.Pxy[0][a][b] = p_at(p, 0, x0 - 1 + b, y0 - 1 + a, kk);
+        sm.Pxy[1][a][b] = p_at(p, 1, x0 - 1 + b, y0 - 1 + a, kk);
+    }
+    for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
+        const int v = t / (BX + 1), u = t - v * (BX + 1);
+        sm.Pz[s][v][u] = p_at(p, 2, x0 + u, y0 + v, kk);
+    }
+    __syncthreads();
+    for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
+        const int v = t / (BX + 1), u = t - v * (BX + 1);
+        sm.D[s][v][u] = (sm.Pxy[0][v + 1][u + 1] - sm.Pxy[0][v + 1][u]) +
+                        (sm.Pxy[1][v + 1][u + 1] - sm.Pxy[1][v][u + 1]) + (sm.Pz[s][v][u] - sm.Pz[s ^ 1][v][u]);
+    }
+    __syncthreads();
+}
+
 // Tile classes (uniform per block): PML = the tile or its halo reaches a
 // CPML slab; TF = it reaches the cells next to the TF/SF surface; MET = it
 // overlaps the metal bounding box.  A tile of none of the classes runs plain
 // Yee arithmetic with no per-cell test.
 template <bool PML, bool TF, bool MET>
-__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1,
-                                      float (*sE)[3][BY + 2][BX + 2], float (*sH)[BY + 1][BX + 1],
-                                      MatCoef* s_coef)
+__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, TileShared& sm)
 {
+    float (*sE)[3][BY + 2][BX + 2] = sm.sE;
+    float (*sH)[BY + 1][BX + 1] = sm.sH;
+    MatCoef* s_coef = sm.coef;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
@@ -446,7 +481,12 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     }
     h_load(p, x0, y0, k0, i, j, in, tid, hr);
     __syncthreads();
+    if (MET) {
+        div_plane(p, sm, x0, y0, k0 - 1, tid);
+        div_plane(p, sm, x0, y0, k0, tid);
+    }
     for (int k = k0; k < k1; ++k) {
+        if (MET) div_plane(p, sm, x0, y0, k + 1, tid);
         const int nx_ = cur ^ 1;
         const bool more = k + 1 < k1;
         // prefetch plane k+2 of E and plane k+1 of H^{n-1/2}
@@ -501,18 +541,25 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
             const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
             if (PML || TF || MET) {
-                float d_here = 0.f;
-                bool d_valid = false;
+                // GD = grad(div P_f^n) from the staged node divergences of planes k and k+1
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+                if (MET) {
+                    const int s0 = k & 1;
+                    const float d0 = sm.D[s0][ty][tx];
+                    gx = sm.D[s0][ty][tx + 1] - d0;
+                    gy = sm.D[s0][ty + 1][tx] - d0;
+                    gz = sm.D[s0 ^ 1][ty][tx] - d0;
+                }
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF, MET>(p, mc, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, d_here, d_valid);
+                    e_cell<0, PML, TF, MET>(p, mc, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, gx);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF, MET>(p, mc, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, d_here, d_valid);
+                    e_cell<1, PML, TF, MET>(p, mc, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, gy);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF, MET>(p, mc, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm, d_here, d_valid);
+                    e_cell<2, PML, TF, MET>(p, mc, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm, gz);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -556,19 +603,14 @@ __device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3],
     *met = m;
 }
 
-struct TileShared {
-    float sE[2][3][BY + 2][BX + 2];
-    float sH[3][BY + 1][BX + 1];
-    MatCoef coef[NLF_MAX_MAT + 1];
-};
 
 template <bool PML, bool TF>
 __device__ __forceinline__ void march_m(const StepParams& p, bool met, int x0, int y0, int k0, int k1, TileShared& sm)
 {
     if (met)
-        march<PML, TF, true>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+        march<PML, TF, true>(p, x0, y0, k0, k1, sm);
     else
-        march<PML, TF, false>(p, x0, y0, k0, k1, sm.sE, sm.sH, sm.coef);
+        march<PML, TF, false>(p, x0, y0, k0, k1, sm);
 }
 
 // One tile (bx, by) and z chunk bz of the fused step; every thread of the

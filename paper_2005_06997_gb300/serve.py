@@ -66,8 +66,27 @@ class Server:
         self.used += nb
         return _Active(req, s, buf, now)
 
+    def _admit_waiting(self, waiting, active, sizes, now):
+        """Admit waiting requests, first in first out, by HBM budget and slots."""
+        while waiting and len(active) < self.max_active:
+            req = waiting[0]
+            key = id(req)
+            if key not in sizes:
+                probe = nlfdtd.Solver(req)
+                sizes[key] = probe.state_bytes()
+                probe.close()
+            if self.used + sizes[key] > self.budget and active:
+                break
+            waiting.popleft()
+            active.append(self._admit(req, now))
+
     def run(self, requests, clock=time.perf_counter):
-        """Serve `requests` (sorted by arrival_s); returns (results, summary)."""
+        """Serve `requests` (sorted by arrival_s); returns (results, summary).
+
+        Each loop iteration enqueues one DFT period of the running batch, then
+        admits the requests that arrived meanwhile on the host while the GPU
+        works (their initialisation is queued behind the period on the same
+        stream), then waits and retires the finished requests."""
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival_s"]))
         waiting = collections.deque()
         active = []
@@ -78,31 +97,27 @@ class Server:
             now = clock() - t0
             while pending and pending[0]["arrival_s"] <= now:
                 waiting.append(pending.popleft())
-            # admission: first in, first out, by HBM budget and batch slots
-            while waiting and len(active) < self.max_active:
-                req = waiting[0]
-                key = id(req)
-                if key not in sizes:
-                    probe = nlfdtd.Solver(req)
-                    sizes[key] = probe.state_bytes()
-                    probe.close()
-                if self.used + sizes[key] > self.budget and active:
-                    break
-                waiting.popleft()
-                active.append(self._admit(req, now))
             if not active:
-                if pending:
-                    time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
-                continue
+                self._admit_waiting(waiting, active, sizes, now)
+                if not active:
+                    if pending:
+                        time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
+                    continue
             U = _period(active[0])
             steps = [min(U, a.remaining) for a in active]
-            before = sum(a.solver.launches for a in active)
-            status = nlfdtd.batch_run([a.solver for a in active], steps, self.stream.cuda_stream)
-            self.stream.synchronize()
-            self.launches += sum(a.solver.launches for a in active) - before
+            running = list(active)
+            before = sum(a.solver.launches for a in running)
+            status = nlfdtd.batch_run([a.solver for a in running], steps, self.stream.cuda_stream)
+            # host work while the GPU runs the period: admit new arrivals
             now = clock() - t0
-            keep = []
-            for a, n, st in zip(active, steps, status):
+            while pending and pending[0]["arrival_s"] <= now:
+                waiting.append(pending.popleft())
+            self._admit_waiting(waiting, active, sizes, now)
+            self.stream.synchronize()
+            self.launches += sum(a.solver.launches for a in running) - before
+            now = clock() - t0
+            done = set()
+            for a, n, st in zip(running, steps, status):
                 a.remaining -= n
                 if st != 0 or a.remaining <= 0:
                     res = {"name": a.req.get("name"), "arrival_s": a.req["arrival_s"], "admit_s": a.admit_s,
@@ -114,9 +129,8 @@ class Server:
                     self.used -= a.solver.state_bytes()
                     a.solver.close()
                     a.buf = None
-                else:
-                    keep.append(a)
-            active = keep
+                    done.add(id(a))
+            active = [a for a in active if id(a) not in done]
         wall = clock() - t0
         return results, summarise(results, wall)
 
