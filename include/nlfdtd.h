@@ -254,6 +254,33 @@ int nlf_load_state(nlf_ctx* ctx, const void* host);
  * (NLF_OK or NLF_E_*).  All contexts must be configured. */
 int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* cuda_stream, int* status_out);
 
+/* Cross sections from running-DFT accumulators that the caller holds in its
+ * own device memory, computed without allocating anything.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc -- device
+ * memory owned by another allocator under a fixed budget, or a loop that must
+ * not take cudaMalloc / cudaFree and the device synchronisation they imply.
+ * The flux partial sums live in a file-scope device array of
+ * NLF_FLUX_STATIC_PAIRS pairs of doubles (2.4 MB) that every GPU loading the
+ * library holds until exit.  All pointers are device pointers:
+ *   acc_e, acc_h  [(n_records + 1)][nf][re, im] doubles, laid out as returned
+ *                 by nlf_get_dft (any common scale factor cancels); the last
+ *                 record is the incident field at the centre plane;
+ *   coef          n_records doubles, the signed face weights of the records
+ *                 (outward sign x term sign x trapezoid weight / 2), in the
+ *                 record order of nlf_get_dft, absorption box records first;
+ *   n_abs         number of absorption-box records;
+ *   dA            face area of one cell, dx^2 (m^2);
+ *   out           4 nf doubles: sigma_ext, sigma_abs, sigma_sca (m^2), I.
+ * Asynchronous on cuda_stream.  The first call on a device looks up the
+ * array's device address once for that device (make it before any stream
+ * capture).  Every call shares the array, which keeps the last call's partial
+ * sums (all are rewritten by each call, none needs clearing); calls that
+ * overlap on the GPU race on it.  Errors: NLF_E_ARG (nf > NLF_FLUX_STATIC_PAIRS,
+ * null pointers, bad sizes), NLF_E_CUDA. */
+#define NLF_FLUX_STATIC_PAIRS 155648
+int nlf_flux_spectra_static(const double* acc_e, const double* acc_h, const double* coef, long long n_abs,
+                            long long n_records, int nf, double dA, double* out, void* cuda_stream);
+
 /* Time index n (E^n, H^{n-1/2} current), sizes, and number of kernels this
  * context has launched (graph replays count each kernel node). */
 long long nlf_time_index(const nlf_ctx* ctx);

@@ -86,6 +86,8 @@ SIGNATURES = {
     "nlf_load_state": (C.c_int, [_P, C.c_void_p]),
     "nlf_batch_run": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_longlong), C.c_void_p,
                                 C.POINTER(C.c_int)]),
+    "nlf_flux_spectra_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int,
+                                          C.c_double, C.c_void_p, C.c_void_p]),
     "nlf_time_index": (C.c_longlong, [_P]),
     "nlf_get_info": (C.c_int, [_P, C.POINTER(nlf_info)]),
     "nlf_kernel_launches": (C.c_longlong, [_P]),
