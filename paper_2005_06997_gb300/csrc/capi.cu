@@ -25,6 +25,7 @@
 
 namespace nlf {
 void launch_step(const StepParams& p, cudaStream_t st);
+void launch_metal(const StepParams& p, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
 void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
                        int slot, const long long* step, int* err, cudaStream_t st);
@@ -33,6 +34,7 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
                  int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
 void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
+void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st);
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st);
 void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
                         int count, cudaStream_t st);
@@ -683,6 +685,10 @@ void step_once(nlf_ctx* c, cudaStream_t st)
 {
     nlf::launch_step(c->sp[c->n & 1], st);
     c->launches += 1;
+    if (c->has_metal) {
+        nlf::launch_metal(c->sp[c->n & 1], st);
+        c->launches += 1;
+    }
     c->n += 1;
     if (c->have_mon && c->n % c->K == 0) {
         const int cur = (int)(c->n & 1);
@@ -746,7 +752,7 @@ struct BatchPlan {
     char* dev = nullptr;              // descriptors (device)
     nlf::BatchStep bs{};
     nlf::BatchDft bd{};
-    long long items = 0, recs = 0, phases = 0, chunks = 0;
+    long long items = 0, met_sites = 0, recs = 0, phases = 0, chunks = 0;
     int max_nf = 0, K = 1, B = 8, U = 128;
     bool mon = false;
     int kz = 0;                       // z chunk used for every instance (0: per-instance heuristic)
@@ -775,9 +781,9 @@ int plan_descriptors(BatchPlan* P, int kz)
     const int n = (int)P->ctxs.size();
     std::vector<nlf::StepParams> params(2 * n);
     std::vector<nlf::BatchInst> inst(n);
-    std::vector<long long> item_end(n), rec_end(n), ph_end(n), chunk_end(n);
+    std::vector<long long> item_end(n), met_end(n), rec_end(n), ph_end(n), chunk_end(n);
     std::vector<nlf::BatchDftInst> dinst(n);
-    long long it = 0, rc = 0, ph = 0, ch = 0;
+    long long it = 0, ms = 0, rc = 0, ph = 0, ch = 0;
     P->max_nf = 0;
     for (int q = 0; q < n; ++q) {
         nlf_ctx* x = P->ctxs[q];
@@ -791,6 +797,8 @@ int plan_descriptors(BatchPlan* P, int kz)
         b.base_par = P->par[q];
         it += (long long)b.tiles_x * b.tiles_y * b.chunks;
         item_end[q] = it;
+        if (x->has_metal) ms += 3 * x->nbb;
+        met_end[q] = ms;
         if (P->mon) {
             nlf::BatchDftInst& d = dinst[q];
             d.d = x->dp;
@@ -814,6 +822,7 @@ int plan_descriptors(BatchPlan* P, int kz)
         chunk_end[q] = ch;
     }
     P->items = it;
+    P->met_sites = ms;
     P->recs = rc;
     P->phases = ph;
     P->chunks = ch;
@@ -826,6 +835,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     const size_t o_par = take(params.size() * sizeof(nlf::StepParams));
     const size_t o_inst = take(inst.size() * sizeof(nlf::BatchInst));
     const size_t o_item = take(n * sizeof(long long));
+    const size_t o_met = take(n * sizeof(long long));
     const size_t o_dinst = take(dinst.size() * sizeof(nlf::BatchDftInst));
     const size_t o_rec = take(n * sizeof(long long));
     const size_t o_ph = take(n * sizeof(long long));
@@ -838,6 +848,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     memcpy(h.data() + o_par, params.data(), params.size() * sizeof(nlf::StepParams));
     memcpy(h.data() + o_inst, inst.data(), inst.size() * sizeof(nlf::BatchInst));
     memcpy(h.data() + o_item, item_end.data(), n * sizeof(long long));
+    memcpy(h.data() + o_met, met_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_dinst, dinst.data(), dinst.size() * sizeof(nlf::BatchDftInst));
     memcpy(h.data() + o_rec, rec_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_ph, ph_end.data(), n * sizeof(long long));
@@ -846,6 +857,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     P->bs.params = reinterpret_cast<const nlf::StepParams*>(P->dev + o_par);
     P->bs.inst = reinterpret_cast<const nlf::BatchInst*>(P->dev + o_inst);
     P->bs.item_end = reinterpret_cast<const long long*>(P->dev + o_item);
+    P->bs.met_end = reinterpret_cast<const long long*>(P->dev + o_met);
     P->bs.n = n;
     P->bd.inst = reinterpret_cast<const nlf::BatchDftInst*>(P->dev + o_dinst);
     P->bd.rec_end = reinterpret_cast<const long long*>(P->dev + o_rec);
@@ -867,6 +879,10 @@ long long plan_launch(BatchPlan* P, cudaStream_t st)
         bs.launch_par = s & 1;
         nlf::launch_step_batch(bs, P->items, st);
         ++nodes;
+        if (P->met_sites > 0) {
+            nlf::launch_metal_batch(bs, P->met_sites, st);
+            ++nodes;
+        }
         if (P->mon && (s + 1) % P->K == 0) {
             nlf::BatchDft bd = P->bd;
             bd.cur_par = (s + 1) & 1;

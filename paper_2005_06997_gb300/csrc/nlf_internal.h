@@ -143,6 +143,7 @@ struct BatchStep {
     const StepParams* params;   // [2 n]
     const BatchInst* inst;      // [n]
     const long long* item_end;  // [n] inclusive prefix sums of work items
+    const long long* met_end;   // [n] inclusive prefix sums of metal-box sites (3 per cell)
     int n;
     int launch_par;
 };

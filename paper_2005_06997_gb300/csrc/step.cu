@@ -156,25 +156,14 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
     return h;
 }
 
-// P_f^n component c at cell (x, y, kk); zero outside the metal box (P_f is
-// zero off the metal, Pekar, and the box carries a two-cell margin).
-__device__ __forceinline__ float p_at(const StepParams& p, int c, int x, int y, int kk)
-{
-    const int bi = x - p.bb_lo[0], bj = y - p.bb_lo[1], bk = kk - p.bb_lo[2];
-    if (bi < 0 || bj < 0 || bk < 0 || bi >= p.bb_n[0] || bj >= p.bb_n[1] || bk >= p.bb_n[2]) return 0.f;
-    const uint32_t b = ((uint32_t)bk * p.bb_n[1] + bj) * p.bb_n[0] + bi;
-    return __ldg(p.P0[c] + b);
-}
-
-// E_C^{n+1} at cell c from E^n = En and H^{n+1/2}: hA2 = H_{A2}(idx),
-// hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2);
-// gd_c = (grad div P_f^n)_C at the site (metal tiles).
+// E_C^{n+1} of the background at cell c from E^n = En and H^{n+1/2}:
+// hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
 // TF: E_x on the planes k = lo_z and k = hi_z, and E_z on the planes
 // i = lo_x and i = hi_x, are total fields reading a scattered H_y.
-// MET: the site may hold a material (coefficient table mc).
-template <int C, bool PML, bool TF, bool MET>
-__device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, const Cell& c, float En, float hA2,
-                                       float hA2m, float hA1, float hA1m, float gd_c)
+// Sites that hold a material are rewritten afterwards by k_metal.
+template <int C, bool PML, bool TF>
+__device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float En, float hA2, float hA2m, float hA1,
+                                       float hA1m)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     if (TF) {
@@ -202,26 +191,39 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, c
             t2 += psi;
         }
     }
-    const float curl = t1 - t2;
-    int id = 0;
-    uint32_t b = 0, sy = 0, sz = 0;
-    if (MET) {
-        const int bi = c.i - p.bb_lo[0], bj = c.j - p.bb_lo[1], bk = c.k - p.bb_lo[2];
-        if (bi >= 0 && bj >= 0 && bk >= 0 && bi < p.bb_n[0] && bj < p.bb_n[1] && bk < p.bb_n[2]) {
-            sy = (uint32_t)p.bb_n[0];
-            sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
-            b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
-            id = p.mat[C][b];
-        }
-    }
-    if (id == 0) {
-        p.E1[C][c.q] = En + p.Sb * curl;
-        return;
-    }
-    const MatCoef& m = mc[id];
+    p.E1[C][c.q] = En + p.Sb * (t1 - t2);
+}
+
+// Node divergence of P_f^n (difference units) at bbox-local offset b.
+__device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint32_t sy, uint32_t sz)
+{
+    return (__ldg(p.P0[0] + b) - __ldg(p.P0[0] + b - 1)) + (__ldg(p.P0[1] + b) - __ldg(p.P0[1] + b - sy)) +
+           (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
+}
+
+// Material update of E-site (C; bi, bj, bk in the metal box) after the fused
+// step: E^{n+1} from Eq. discreteamperes with f3 and f4 substituted (increment
+// form), then P_CP^{n+1} and P_f^{n+1}.  The curl uses H^{n+1/2} just written
+// by the step (material sites lie at least two cells inside the TF box and
+// outside the CPML, so neither correction applies there).
+template <int C>
+__device__ __forceinline__ void metal_site(const StepParams& p, int bi, int bj, int bk)
+{
+    constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
+    const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
+    const uint32_t b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
+    const int id = p.mat[C][b];
+    if (id == 0) return;
+    const int i = p.bb_lo[0] + bi, j = p.bb_lo[1] + bj, k = p.bb_lo[2] + bk;
+    const uint32_t st[3] = {1u, (uint32_t)p.nx, (uint32_t)p.nx * (uint32_t)p.ny};
+    const uint32_t q = (uint32_t)k * st[2] + (uint32_t)j * st[1] + (uint32_t)i;
+    const float curl = (p.H1[A2][q] - p.H1[A2][q - st[A1]]) - (p.H1[A1][q] - p.H1[A1][q - st[A2]]);
+    const float En = __ldg(p.E0[C] + q);
+    const MatCoef& m = p.coef[id];
     float gd = 0.f, af = 0.f;
     if (m.free_e) {
-        gd = gd_c;
+        const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
+        gd = node_div(p, b + stb, sy, sz) - node_div(p, b, sy, sz);
         af = p.auxf[C][b];
     }
     float ac[NLF_MAX_POLES];
@@ -232,7 +234,7 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, c
         acs += ac[pp];
     }
     const float delta = (p.S * curl - af - acs - m.G * gd - m.cE * En) * m.inv_den;
-    p.E1[C][c.q] = En + delta;
+    p.E1[C][q] = En + delta;
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
         p.P1[C][b] = __ldg(p.P0[C] + b) + dP;
@@ -252,6 +254,30 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const MatCoef* mc, c
         p.pcp[pp][C][b] = pc;
         p.auxcp[pp][C][b] = -m.kap[pp] * pc - m.C2[pp] * dPc + m.C5[pp] * En;
     }
+}
+
+// Site t of the metal box (component-major, x fastest).
+__device__ __forceinline__ void metal_item(const StepParams& p, long long t)
+{
+    const long long nb = (long long)p.bb_n[0] * p.bb_n[1] * p.bb_n[2];
+    const int c = (int)(t / nb);
+    const long long r = t - c * nb;
+    const int bi = (int)(r % p.bb_n[0]);
+    const long long rr = r / p.bb_n[0];
+    const int bj = (int)(rr % p.bb_n[1]);
+    const int bk = (int)(rr / p.bb_n[1]);
+    if (c == 0)
+        metal_site<0>(p, bi, bj, bk);
+    else if (c == 1)
+        metal_site<1>(p, bi, bj, bk);
+    else
+        metal_site<2>(p, bi, bj, bk);
+}
+
+__global__ void __launch_bounds__(256) k_metal(const StepParams p)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 3LL * p.bb_n[0] * p.bb_n[1] * p.bb_n[2]) metal_item(p, t);
 }
 
 __device__ double source_value(const StepParams& p, double t)
@@ -395,60 +421,20 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
 struct TileShared {
     float sE[2][3][BY + 2][BX + 2];
     float sH[3][BY + 1][BX + 1];
-    MatCoef coef[NLF_MAX_MAT + 1];
-    // metal tiles: P_x, P_y of one plane at x0-1..x0+BX, y0-1..y0+BY; P_z and
-    // the node divergence of two planes (by parity) at x0..x0+BX, y0..y0+BY
-    float Pxy[2][BY + 2][BX + 2];
-    float Pz[2][BY + 1][BX + 1];
-    float D[2][BY + 1][BX + 1];
 };
 
-// Node divergence of P_f^n (difference units) for plane kk into slot kk & 1:
-// d(x, y) = P_x(x) - P_x(x-1) + P_y(y) - P_y(y-1) + P_z(kk) - P_z(kk-1) at the
-// nodes x0..x0+BX, y0..y0+BY (P_z(kk-1) is the other slot, staged before).
-__device__ __forceinline__ void div_plane(const StepParams& p, TileShared& sm, int x0, int y0, int kk, int tid)
-{
-    const int s = kk & 1;
-    for (int t = tid; t < (BY + 2) * (BX + 2); t += BX * BY) {
-        const int a = t / (BX + 2), b = t - a * (BX + 2);
-        sm.Pxy[0][a][b] = p_at(p, 0, x0 - 1 + b, y0 - 1 + a, kk);
-        sm.Pxy[1][a][b] = p_at(p, 1, x0 - 1 + b, y0 - 1 + a, kk);
-    }
-    for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
-        const int v = t / (BX + 1), u = t - v * (BX + 1);
-        sm.Pz[s][v][u] = p_at(p, 2, x0 + u, y0 + v, kk);
-    }
-    __syncthreads();
-    for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
-        const int v = t / (BX + 1), u = t - v * (BX + 1);
-        sm.D[s][v][u] = (sm.Pxy[0][v + 1][u + 1] - sm.Pxy[0][v + 1][u]) +
-                        (sm.Pxy[1][v + 1][u + 1] - sm.Pxy[1][v][u + 1]) + (sm.Pz[s][v][u] - sm.Pz[s ^ 1][v][u]);
-    }
-    __syncthreads();
-}
-
 // Tile classes (uniform per block): PML = the tile or its halo reaches a
-// CPML slab; TF = it reaches the cells next to the TF/SF surface; MET = it
-// overlaps the metal bounding box.  A tile of none of the classes runs plain
-// Yee arithmetic with no per-cell test.
-template <bool PML, bool TF, bool MET>
+// CPML slab; TF = it reaches the cells next to the TF/SF surface.  A tile of
+// neither class runs plain Yee arithmetic with no per-cell test.
+template <bool PML, bool TF>
 __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, TileShared& sm)
 {
     float (*sE)[3][BY + 2][BX + 2] = sm.sE;
     float (*sH)[BY + 1][BX + 1] = sm.sH;
-    MatCoef* s_coef = sm.coef;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
     const int lx = tx + 1, ly = ty + 1;
-    const MatCoef* mc = p.coef;
-    if (MET) {
-        const int nw = (int)((NLF_MAX_MAT + 1) * sizeof(MatCoef) / sizeof(int));
-        const int* src = reinterpret_cast<const int*>(p.coef);
-        int* dst = reinterpret_cast<int*>(s_coef);
-        for (int t = tid; t < nw; t += BX * BY) dst[t] = src[t];
-        mc = s_coef;
-    }
     // slab positions of the own column and of the halo cells (constant along z)
     const int slx = PML ? slab_local(p, 0, i) : -1, sly = PML ? slab_local(p, 1, j) : -1;
     float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
@@ -481,12 +467,7 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     }
     h_load(p, x0, y0, k0, i, j, in, tid, hr);
     __syncthreads();
-    if (MET) {
-        div_plane(p, sm, x0, y0, k0 - 1, tid);
-        div_plane(p, sm, x0, y0, k0, tid);
-    }
     for (int k = k0; k < k1; ++k) {
-        if (MET) div_plane(p, sm, x0, y0, k + 1, tid);
         const int nx_ = cur ^ 1;
         const bool more = k + 1 < k1;
         // prefetch plane k+2 of E and plane k+1 of H^{n-1/2}
@@ -540,26 +521,17 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         if (in) {
             const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
             const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
-            if (PML || TF || MET) {
-                // GD = grad(div P_f^n) from the staged node divergences of planes k and k+1
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-                if (MET) {
-                    const int s0 = k & 1;
-                    const float d0 = sm.D[s0][ty][tx];
-                    gx = sm.D[s0][ty][tx + 1] - d0;
-                    gy = sm.D[s0][ty + 1][tx] - d0;
-                    gz = sm.D[s0 ^ 1][ty][tx] - d0;
-                }
+            if (PML || TF) {
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF, MET>(p, mc, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev, gx);
+                    e_cell<0, PML, TF>(p, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF, MET>(p, mc, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi, gy);
+                    e_cell<1, PML, TF>(p, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF, MET>(p, mc, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm, gz);
+                    e_cell<2, PML, TF>(p, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -582,13 +554,13 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
 }
 
 // Classes of the box [lo, hi] (cells, inclusive): does it touch a CPML slab,
-// a cell on which a TF/SF conversion happens (within one cell of the TF
-// surface), or the metal box?
+// or a cell on which a TF/SF conversion happens (within one cell of the TF
+// surface)?
 __device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3], const int hi[3], bool* pml,
-                                           bool* tf, bool* met)
+                                           bool* tf)
 {
     const int n3[3] = {p.nx, p.ny, p.nz};
-    bool b = false, m = p.has_metal != 0;
+    bool b = false;
     bool inner = true, outer = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -596,21 +568,9 @@ __device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3],
         // every conversion sits on the planes tf_lo - 1 .. tf_lo or tf_hi .. (tf_hi) of some axis
         if (!(lo[a] > p.tf_lo[a] && hi[a] < p.tf_hi[a] - 1)) inner = false;
         if (hi[a] < p.tf_lo[a] - 1 || lo[a] > p.tf_hi[a]) outer = true;
-        if (hi[a] < p.bb_lo[a] || lo[a] >= p.bb_lo[a] + p.bb_n[a]) m = false;
     }
     *pml = b;
     *tf = p.tfsf && !inner && !outer;
-    *met = m;
-}
-
-
-template <bool PML, bool TF>
-__device__ __forceinline__ void march_m(const StepParams& p, bool met, int x0, int y0, int k0, int k1, TileShared& sm)
-{
-    if (met)
-        march<PML, TF, true>(p, x0, y0, k0, k1, sm);
-    else
-        march<PML, TF, false>(p, x0, y0, k0, k1, sm);
 }
 
 // One tile (bx, by) and z chunk bz of the fused step; every thread of the
@@ -622,18 +582,18 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, i
     const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
-    bool pml, tf, met;
-    tile_class(p, lo, hi, &pml, &tf, &met);
+    bool pml, tf;
+    tile_class(p, lo, hi, &pml, &tf);
     if (pml) {
         if (tf)
-            march_m<true, true>(p, met, x0, y0, k0, k1, sm);
+            march<true, true>(p, x0, y0, k0, k1, sm);
         else
-            march_m<true, false>(p, met, x0, y0, k0, k1, sm);
+            march<true, false>(p, x0, y0, k0, k1, sm);
     } else {
         if (tf)
-            march_m<false, true>(p, met, x0, y0, k0, k1, sm);
+            march<false, true>(p, x0, y0, k0, k1, sm);
         else
-            march_m<false, false>(p, met, x0, y0, k0, k1, sm);
+            march<false, false>(p, x0, y0, k0, k1, sm);
     }
     if (bx == 0 && by == 0 && bz == 0) {
         const int tid = threadIdx.y * BX + threadIdx.x;
@@ -716,6 +676,31 @@ void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t s
 {
     const long long g = total_items < batch_blocks() ? total_items : batch_blocks();
     k_step_batch<<<(unsigned)g, dim3(BX, BY, 1), 0, st>>>(a);
+}
+
+// Batched material update: grid-stride over every instance's metal-box sites.
+__global__ void __launch_bounds__(256) k_metal_batch(const BatchStep a)
+{
+    const long long total = a.met_end[a.n - 1];
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int q = find_inst(a.met_end, a.n, w);
+        const int par = a.inst[q].base_par ^ a.launch_par;
+        metal_item(a.params[2 * q + par], w - (q > 0 ? a.met_end[q - 1] : 0));
+    }
+}
+
+void launch_metal(const StepParams& p, cudaStream_t st)
+{
+    const long long n = 3LL * p.bb_n[0] * p.bb_n[1] * p.bb_n[2];
+    k_metal<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p);
+}
+
+void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st)
+{
+    long long g = (total_sites + 255) / 256;
+    if (g > 152LL * 16) g = 152LL * 16;
+    k_metal_batch<<<(unsigned)g, 256, 0, st>>>(a);
 }
 
 int step_kz(const StepParams& p)

@@ -1,11 +1,14 @@
 """Run a named workload for a few time steps (the command that profiles are
-taken on: ``python -m paper_2005_06997_gb300.profile_run <workload> <steps> [nf]``).
+taken on: ``python -m paper_2005_06997_gb300.profile_run <workload> <steps> [nf]
+[pec] [nosource] [nometal]``).
 
 It configures the problem through the C ABI, runs `steps` time steps, reads
 the spectra and prints the launch count.  The kernels and the problem are the
 benchmark's; only the number of time steps and, if given, the number of DFT
 frequencies (every nf-th of the 200, to keep a profiler's memory save/restore
-small; the time-step kernel does not depend on it) differ.
+small; the time-step kernel does not depend on it) differ.  The words pec,
+nosource and nometal select the same grid with PEC walls instead of the CPML,
+without the TF/SF source and monitors, or without the particle.
 """
 import sys
 
@@ -24,12 +27,23 @@ def main():
         nf = int(sys.argv[3])
         om = prob["monitors"]["omega"]
         prob["monitors"]["omega"] = om[:: max(1, len(om) // nf)][:nf]
+    words = set(sys.argv[4:])
+    if "pec" in words:
+        prob["bc"] = ("pec",) * 3
+    if "nosource" in words:
+        prob["source"] = None
+        prob["monitors"] = None
+    if "nometal" in words:
+        prob["shapes"] = []
     s = nlfdtd.Solver(prob)
     s.run(steps)
     s.sync()
-    spec = s.spectra()
-    print("%s: %d steps, %d kernel launches, state %.2f GB, finite spectra %s" %
-          (name, steps, s.launches, s.state_bytes() / 1e9, bool((spec["ext"] == spec["ext"]).all())))
+    fin = None
+    if prob.get("monitors") is not None:
+        spec = s.spectra()
+        fin = bool((spec["ext"] == spec["ext"]).all())
+    print("%s %s: %d steps, %d kernel launches, state %.2f GB, finite spectra %s" %
+          (name, " ".join(sorted(words)), steps, s.launches, s.state_bytes() / 1e9, fin))
 
 
 if __name__ == "__main__":
