@@ -55,6 +55,34 @@ __global__ void k_voxelise(const VoxParams v)
     if (id != 0 && v.free_e[id]) atomicAdd(&v.counts[c], 1ULL);
 }
 
+// Compact list of the E-sites of the metal box that hold a material, entry
+// (component << 30) | box offset.  Each warp reserves its run with one atomic,
+// so runs land in any order while each run keeps box order; the material
+// update is independent per site, so the order does not change any result.
+__global__ void k_site_list(const uint8_t* __restrict__ mat, long long n3, uint32_t* sites, long long nb,
+                            unsigned long long* count)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = t < n3 && mat[t] != 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    if (mask == 0u) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has) {
+        const uint32_t c = (uint32_t)(t / nb);
+        const uint32_t b = (uint32_t)(t - (long long)c * nb);
+        sites[base + __popc(mask & ((1u << lane) - 1u))] = (c << 30) | b;
+    }
+}
+
+void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st)
+{
+    const long long n = 3 * nb;
+    k_site_list<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mat, n, sites, nb, count);
+}
+
 void launch_voxelise(const VoxParams& v, cudaStream_t st)
 {
     const long long nb = (long long)v.bb_n[0] * v.bb_n[1] * v.bb_n[2];

@@ -25,7 +25,8 @@
 
 namespace nlf {
 void launch_step(const StepParams& p, cudaStream_t st);
-void launch_metal(const StepParams& p, cudaStream_t st);
+void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
+void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
 void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
                        int slot, const long long* step, int* err, cudaStream_t st);
@@ -76,6 +77,7 @@ struct nlf_ctx {
     bool has_metal = false;
     int bb_lo[3] = {0, 0, 0}, bb_n[3] = {0, 0, 0};
     long long nbb = 0;
+    long long n_msites = 0;     // E-sites of the metal box that hold a material
     int inc_off = 0, inc_len = 0, inc_node = 0;
     int K = 1, B = 16, U = 128;
     long long nrec = 0, n_abs = 0;
@@ -94,6 +96,7 @@ struct nlf_ctx {
     size_t off_psiE[3] = {0, 0, 0}, off_psiH[2][3] = {{0, 0, 0}, {0, 0, 0}};
     size_t off_prof[3] = {0, 0, 0};
     size_t off_inc = 0;
+    size_t off_sites = 0;
     size_t off_mat = 0, off_P[2] = {0, 0}, off_auxf = 0, off_gdp = 0, off_pcp = 0, off_auxcp = 0, off_coef = 0,
            off_free = 0, off_counts = 0;
     size_t off_rec = 0, off_dcoef = 0, off_omega = 0, off_samples = 0, off_sstep = 0, off_phase = 0, off_acc = 0,
@@ -335,6 +338,8 @@ int plan(nlf_ctx* c)
                 return fail(c, NLF_E_GEOMETRY, "metal reaches the CPML or the wall on axis %d", a);
         }
         c->nbb = (long long)c->bb_n[0] * c->bb_n[1] * c->bb_n[2];
+        if (c->nbb >= (1LL << 30))
+            return fail(c, NLF_E_GEOMETRY, "metal bounding box of %lld cells exceeds 2^30", c->nbb);
     }
     if (c->have_src) {
         int rc = check_boxes(c);
@@ -389,10 +394,11 @@ int plan(nlf_ctx* c)
     if (c->have_src) c->off_inc = take(10 * (size_t)c->inc_len * sizeof(float));
     c->off_coef = take((NLF_MAX_MAT + 1) * sizeof(nlf::MatCoef));
     c->off_free = take((NLF_MAX_MAT + 1) * sizeof(int));
-    c->off_counts = take(3 * sizeof(unsigned long long));
+    c->off_counts = take(4 * sizeof(unsigned long long));
     if (c->has_metal) {
         const size_t nb = (size_t)c->nbb;
         c->off_mat = take(3 * nb);
+        c->off_sites = take(3 * nb * sizeof(uint32_t));
         c->off_P[0] = take(3 * nb * sizeof(float));
         c->off_P[1] = take(3 * nb * sizeof(float));
         c->off_auxf = take(3 * nb * sizeof(float));
@@ -493,6 +499,7 @@ void fill_params(nlf_ctx* c)
             }
             for (int k = 0; k < 3; ++k) {
                 p.mat[k] = at<uint8_t>(c, c->off_mat) + k * nb;
+                p.sites = at<uint32_t>(c, c->off_sites);
                 p.P0[k] = at<float>(c, c->off_P[r]) + k * nb;
                 p.P1[k] = at<float>(c, c->off_P[w]) + k * nb;
                 p.auxf[k] = at<float>(c, c->off_auxf) + k * nb;
@@ -639,15 +646,22 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         if ((rc = put(c->off_dcoef, co.data(), co.size() * sizeof(double)))) return rc;
         if ((rc = put(c->off_omega, c->omega.data(), c->omega.size() * sizeof(double)))) return rc;
     }
+    if (c->has_metal) {
+        nlf::launch_site_list(at<uint8_t>(c, c->off_mat), c->nbb, at<uint32_t>(c, c->off_sites),
+                              at<unsigned long long>(c, c->off_counts) + 3, st);
+        CK(cudaGetLastError());
+        c->launches += 1;
+    }
     fill_params(c);
     // info
-    unsigned long long cnts[3] = {0, 0, 0};
+    unsigned long long cnts[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(cnts, c->base + c->off_counts, sizeof cnts, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->d2h += (long long)sizeof cnts;
     nlf_info& in = c->info;
     in.cells = c->ncell;
     in.metal_sites = (long long)(cnts[0] + cnts[1] + cnts[2]);
+    c->n_msites = (long long)cnts[3];
     in.pole_sites = c->max_poles > 0 ? in.metal_sites : 0;
     in.bbox_cells = c->nbb;
     in.pml_slab_cells = c->pml_slab[0] + c->pml_slab[1] + c->pml_slab[2];
@@ -685,8 +699,8 @@ void step_once(nlf_ctx* c, cudaStream_t st)
 {
     nlf::launch_step(c->sp[c->n & 1], st);
     c->launches += 1;
-    if (c->has_metal) {
-        nlf::launch_metal(c->sp[c->n & 1], st);
+    if (c->n_msites > 0) {
+        nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
         c->launches += 1;
     }
     c->n += 1;
@@ -797,7 +811,7 @@ int plan_descriptors(BatchPlan* P, int kz)
         b.base_par = P->par[q];
         it += (long long)b.tiles_x * b.tiles_y * b.chunks;
         item_end[q] = it;
-        if (x->has_metal) ms += 3 * x->nbb;
+        if (x->has_metal) ms += x->n_msites;
         met_end[q] = ms;
         if (P->mon) {
             nlf::BatchDftInst& d = dinst[q];

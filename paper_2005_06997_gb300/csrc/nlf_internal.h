@@ -90,6 +90,7 @@ struct StepParams {
     int has_metal;
     int bb_lo[3], bb_n[3];
     const uint8_t* mat[3];
+    const uint32_t* sites;      // material E-sites of the box: (component << 30) | box offset
     const MatCoef* coef;        // [n_materials + 1], index 0 unused
     const float* P0[3];
     float* P1[3];

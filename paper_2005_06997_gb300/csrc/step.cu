@@ -201,46 +201,54 @@ __device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint3
            (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
 }
 
-// Material update of E-site (C; bi, bj, bk in the metal box) after the fused
-// step: E^{n+1} from Eq. discreteamperes with f3 and f4 substituted (increment
-// form), then P_CP^{n+1} and P_f^{n+1}.  The curl uses H^{n+1/2} just written
-// by the step (material sites lie at least two cells inside the TF box and
-// outside the CPML, so neither correction applies there).
+// Material update of E-site (C, box offset b) after the EM step: E^{n+1}
+// from Eq. discreteamperes with f3 and f4 substituted (increment form), then
+// P_CP^{n+1} and P_f^{n+1}.  The curl uses H^{n+1/2} just written by the step
+// (material sites lie at least two cells inside the TF box and outside the
+// CPML, so neither correction applies there).  Every operand is loaded before
+// the material's coefficients are consulted, so one memory round trip serves
+// the whole site; arrays a material does not use are read and ignored.
 template <int C>
-__device__ __forceinline__ void metal_site(const StepParams& p, int bi, int bj, int bk)
+__device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
-    const uint32_t b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
-    const int id = p.mat[C][b];
-    if (id == 0) return;
-    const int i = p.bb_lo[0] + bi, j = p.bb_lo[1] + bj, k = p.bb_lo[2] + bk;
+    const uint32_t bk = b / sz, r = b - bk * sz, bj = r / sy, bi = r - bj * sy;
     const uint32_t st[3] = {1u, (uint32_t)p.nx, (uint32_t)p.nx * (uint32_t)p.ny};
-    const uint32_t q = (uint32_t)k * st[2] + (uint32_t)j * st[1] + (uint32_t)i;
-    const float curl = (p.H1[A2][q] - p.H1[A2][q - st[A1]]) - (p.H1[A1][q] - p.H1[A1][q - st[A2]]);
+    const uint32_t q = (uint32_t)(p.bb_lo[2] + (int)bk) * st[2] + (uint32_t)(p.bb_lo[1] + (int)bj) * st[1] +
+                       (uint32_t)(p.bb_lo[0] + (int)bi);
+    const int id = __ldg(p.mat[C] + b);
+    const float h2 = p.H1[A2][q], h2m = p.H1[A2][q - st[A1]];
+    const float h1 = p.H1[A1][q], h1m = p.H1[A1][q - st[A2]];
     const float En = __ldg(p.E0[C] + q);
-    const MatCoef& m = p.coef[id];
-    float gd = 0.f, af = 0.f;
-    if (m.free_e) {
-        const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
-        gd = node_div(p, b + stb, sy, sz) - node_div(p, b, sy, sz);
-        af = p.auxf[C][b];
+    const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
+    const float gd_raw = node_div(p, b + stb, sy, sz) - node_div(p, b, sy, sz);
+    const float p_old = __ldg(p.P0[C] + b);
+    const float af_raw = p.auxf[C][b];
+    const float g1 = p.any_gnor ? p.gdp[C][b] : 0.f;
+    float ac[NLF_MAX_POLES], pc[NLF_MAX_POLES];
+#pragma unroll
+    for (int pp = 0; pp < NLF_MAX_POLES; ++pp) {
+        ac[pp] = pp < p.max_poles ? p.auxcp[pp][C][b] : 0.f;
+        pc[pp] = pp < p.max_poles ? p.pcp[pp][C][b] : 0.f;
     }
-    float ac[NLF_MAX_POLES];
+    const MatCoef& m = p.coef[id];
+    const float curl = (h2 - h2m) - (h1 - h1m);
+    const float gd = m.free_e ? gd_raw : 0.f;
+    const float af = m.free_e ? af_raw : 0.f;
     float acs = 0.f;
 #pragma unroll
     for (int pp = 0; pp < NLF_MAX_POLES; ++pp) {
-        ac[pp] = pp < m.npoles ? p.auxcp[pp][C][b] : 0.f;
+        if (pp >= m.npoles) ac[pp] = 0.f;
         acs += ac[pp];
     }
     const float delta = (p.S * curl - af - acs - m.G * gd - m.cE * En) * m.inv_den;
     p.E1[C][q] = En + delta;
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
-        p.P1[C][b] = __ldg(p.P0[C] + b) + dP;
+        p.P1[C][b] = p_old + dP;
         float a_new = -m.D2 * dP + m.D3 * En;
         if (m.gnor) {
-            const float g1 = p.gdp[C][b];
             a_new += m.DG2 * (g1 - 4.f * gd);
             p.gdp[C][b] = gd;
         }
@@ -250,34 +258,28 @@ __device__ __forceinline__ void metal_site(const StepParams& p, int bi, int bj, 
     for (int pp = 0; pp < NLF_MAX_POLES; ++pp) {
         if (pp >= m.npoles) break;
         const float dPc = ac[pp] + m.C3[pp] * (En + delta) + m.C4[pp] * En;
-        const float pc = p.pcp[pp][C][b] + dPc;
-        p.pcp[pp][C][b] = pc;
-        p.auxcp[pp][C][b] = -m.kap[pp] * pc - m.C2[pp] * dPc + m.C5[pp] * En;
+        const float pcn = pc[pp] + dPc;
+        p.pcp[pp][C][b] = pcn;
+        p.auxcp[pp][C][b] = -m.kap[pp] * pcn - m.C2[pp] * dPc + m.C5[pp] * En;
     }
 }
 
-// Site t of the metal box (component-major, x fastest).
-__device__ __forceinline__ void metal_item(const StepParams& p, long long t)
+// Entry e of the material site list.
+__device__ __forceinline__ void metal_entry(const StepParams& p, uint32_t e)
 {
-    const long long nb = (long long)p.bb_n[0] * p.bb_n[1] * p.bb_n[2];
-    const int c = (int)(t / nb);
-    const long long r = t - c * nb;
-    const int bi = (int)(r % p.bb_n[0]);
-    const long long rr = r / p.bb_n[0];
-    const int bj = (int)(rr % p.bb_n[1]);
-    const int bk = (int)(rr / p.bb_n[1]);
+    const uint32_t c = e >> 30, b = e & 0x3fffffffu;
     if (c == 0)
-        metal_site<0>(p, bi, bj, bk);
+        metal_site<0>(p, b);
     else if (c == 1)
-        metal_site<1>(p, bi, bj, bk);
+        metal_site<1>(p, b);
     else
-        metal_site<2>(p, bi, bj, bk);
+        metal_site<2>(p, b);
 }
 
-__global__ void __launch_bounds__(256) k_metal(const StepParams p)
+__global__ void __launch_bounds__(256) k_metal(const StepParams p, long long n_sites)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 3LL * p.bb_n[0] * p.bb_n[1] * p.bb_n[2]) metal_item(p, t);
+    if (t < n_sites) metal_entry(p, __ldg(p.sites + t));
 }
 
 __device__ double source_value(const StepParams& p, double t)
@@ -418,9 +420,14 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
     }
 }
 
+// Three E planes (k, k+1 and the one being filled with k+2) and two H planes
+// (written at k, read by the E update of k) let each z step run with one
+// block barrier: the store of plane k+2 goes to the buffer of plane k-1, read
+// last before the previous barrier, and the H plane of k+1 goes to the buffer
+// read last by the E update of k-1.
 struct TileShared {
-    float sE[2][3][BY + 2][BX + 2];
-    float sH[3][BY + 1][BX + 1];
+    float sE[3][3][BY + 2][BX + 2];
+    float sH[2][3][BY + 1][BX + 1];
 };
 
 // Tile classes (uniform per block): PML = the tile or its halo reaches a
@@ -430,7 +437,6 @@ template <bool PML, bool TF>
 __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, TileShared& sm)
 {
     float (*sE)[3][BY + 2][BX + 2] = sm.sE;
-    float (*sH)[BY + 1][BX + 1] = sm.sH;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
@@ -440,35 +446,29 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
     PlaneRegs pr;
     HRegs hr = {{0.f, 0.f, 0.f}, {0.f, 0.f}};
-    int cur;
+    // buffers of planes k (cur), k+1 (nxt) and k-1 / k+2 (fre)
+    int cur = 0, nxt = 1, fre = 2;
+    plane_load(p, x0, y0, k0, tx, ty, tid, pr);
+    plane_store(sE[cur], pr, x0, y0, tx, ty, tid);
+    plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
+    plane_store(sE[nxt], pr, x0, y0, tx, ty, tid);
     if (k0 > 0) {
         plane_load(p, x0, y0, k0 - 1, tx, ty, tid, pr);
-        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
-        plane_load(p, x0, y0, k0, tx, ty, tid, pr);
-        plane_store(sE[1], pr, x0, y0, tx, ty, tid);
+        plane_store(sE[fre], pr, x0, y0, tx, ty, tid);
         __syncthreads();
         if (in) {
             const Cell c = make_cell(p, i, j, k0 - 1, PML);
-            hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), sE[0][2][ly][lx], sE[0][2][ly + 1][lx],
-                                         sE[0][1][ly][lx], sE[1][1][ly][lx], false);
-            hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), sE[0][0][ly][lx], sE[1][0][ly][lx],
-                                         sE[0][2][ly][lx], sE[0][2][ly][lx + 1], false);
+            hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), sE[fre][2][ly][lx], sE[fre][2][ly + 1][lx],
+                                         sE[fre][1][ly][lx], sE[cur][1][ly][lx], false);
+            hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), sE[fre][0][ly][lx], sE[cur][0][ly][lx],
+                                         sE[fre][2][ly][lx], sE[fre][2][ly][lx + 1], false);
         }
-        __syncthreads();
-        plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
-        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
-        cur = 1;
-    } else {
-        plane_load(p, x0, y0, k0, tx, ty, tid, pr);
-        plane_store(sE[0], pr, x0, y0, tx, ty, tid);
-        plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
-        plane_store(sE[1], pr, x0, y0, tx, ty, tid);
-        cur = 0;
     }
     h_load(p, x0, y0, k0, i, j, in, tid, hr);
     __syncthreads();
+    int hb = 0;
     for (int k = k0; k < k1; ++k) {
-        const int nx_ = cur ^ 1;
+        float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
         const bool more = k + 1 < k1;
         // prefetch plane k+2 of E and plane k+1 of H^{n-1/2}
         HRegs hn = hr;
@@ -486,11 +486,14 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         c.l[2] = PML ? slab_local(p, 2, k) : -1;
         if (PML) cell_slabs(p, c);
         float hx = 0.f, hy = 0.f, hz = 0.f;
+        float ex = 0.f, ey = 0.f, ez = 0.f;
         // f1: own H^{n+1/2}
         if (in) {
-            const float ex = sE[cur][0][ly][lx], ey = sE[cur][1][ly][lx], ez = sE[cur][2][ly][lx];
-            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nx_][1][ly][lx], true);
-            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nx_][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
+            ex = sE[cur][0][ly][lx];
+            ey = sE[cur][1][ly][lx];
+            ez = sE[cur][2][ly][lx];
+            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nxt][1][ly][lx], true);
+            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nxt][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
             hz = h_cell<2, PML, TF>(p, c, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true);
             sH[0][ly][lx] = hx;
             sH[1][ly][lx] = hy;
@@ -501,7 +504,7 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             const int jh = y0 + tid, sy = tid + 1;
             if (x0 > 0 && jh < p.ny) {
                 const Cell h = make_cell(p, x0 - 1, jh, k, PML);
-                sH[1][sy][0] = h_cell<1, PML, TF>(p, h, hr.halo[0], sE[cur][0][sy][0], sE[nx_][0][sy][0],
+                sH[1][sy][0] = h_cell<1, PML, TF>(p, h, hr.halo[0], sE[cur][0][sy][0], sE[nxt][0][sy][0],
                                                   sE[cur][2][sy][0], sE[cur][2][sy][1], false);
                 sH[2][sy][0] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
                                                   sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false);
@@ -511,45 +514,45 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             if (y0 > 0 && ih < p.nx) {
                 const Cell h = make_cell(p, ih, y0 - 1, k, PML);
                 sH[0][0][sx] = h_cell<0, PML, TF>(p, h, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
-                                                  sE[cur][1][0][sx], sE[nx_][1][0][sx], false);
+                                                  sE[cur][1][0][sx], sE[nxt][1][0][sx], false);
                 sH[2][0][sx] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
                                                   sE[cur][0][0][sx], sE[cur][0][1][sx], false);
             }
         }
+        if (more) plane_store(sE[fre], pr, x0, y0, tx, ty, tid);
         __syncthreads();
-        // f2, f3, f4 on the tile; tangential E on the walls stays zero
+        // f2, f3, f4 on the tile (reads only sH and registers); tangential E on the walls stays zero
         if (in) {
             const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
             const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
             if (PML || TF) {
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF>(p, c, sE[cur][0][ly][lx], hz, hzm, hy, hy_prev);
+                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF>(p, c, sE[cur][1][ly][lx], hx, hx_prev, hz, hzi);
+                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF>(p, c, sE[cur][2][ly][lx], hy, hyi, hx, hxm);
+                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
                 // background: eps_b dE = S curl H
-                p.E1[0][c.q] = (j >= 1 && k >= 1) ? sE[cur][0][ly][lx] + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
-                p.E1[1][c.q] = (i >= 1 && k >= 1) ? sE[cur][1][ly][lx] + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
-                p.E1[2][c.q] = (i >= 1 && j >= 1) ? sE[cur][2][ly][lx] + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
+                p.E1[0][c.q] = (j >= 1 && k >= 1) ? ex + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
+                p.E1[1][c.q] = (i >= 1 && k >= 1) ? ey + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
+                p.E1[2][c.q] = (i >= 1 && j >= 1) ? ez + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
             }
         }
         hx_prev = hx;
         hy_prev = hy;
         hr = hn;
-        __syncthreads();
-        if (more) {
-            plane_store(sE[cur], pr, x0, y0, tx, ty, tid);
-            __syncthreads();
-        }
-        cur = nx_;
+        const int t = cur;
+        cur = nxt;
+        nxt = fre;
+        fre = t;
+        hb ^= 1;
     }
 }
 
@@ -678,28 +681,32 @@ void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t s
     k_step_batch<<<(unsigned)g, dim3(BX, BY, 1), 0, st>>>(a);
 }
 
-// Batched material update: grid-stride over every instance's metal-box sites.
+// Batched material update: grid-stride over the material site lists of every
+// instance (prefix sums met_end).
 __global__ void __launch_bounds__(256) k_metal_batch(const BatchStep a)
 {
-    const long long total = a.met_end[a.n - 1];
+    __shared__ long long s_end[NLF_MAX_BATCH];
+    for (int q = threadIdx.x; q < a.n; q += blockDim.x) s_end[q] = a.met_end[q];
+    __syncthreads();
+    const long long total = s_end[a.n - 1];
     for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total;
          w += (long long)gridDim.x * blockDim.x) {
-        const int q = find_inst(a.met_end, a.n, w);
-        const int par = a.inst[q].base_par ^ a.launch_par;
-        metal_item(a.params[2 * q + par], w - (q > 0 ? a.met_end[q - 1] : 0));
+        const int q = find_inst(s_end, a.n, w);
+        const StepParams& p = a.params[2 * q + (a.inst[q].base_par ^ a.launch_par)];
+        metal_entry(p, __ldg(p.sites + (w - (q > 0 ? s_end[q - 1] : 0))));
     }
 }
 
-void launch_metal(const StepParams& p, cudaStream_t st)
+void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st)
 {
-    const long long n = 3LL * p.bb_n[0] * p.bb_n[1] * p.bb_n[2];
-    k_metal<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p);
+    if (n_sites <= 0) return;
+    k_metal<<<(unsigned)((n_sites + 255) / 256), 256, 0, st>>>(p, n_sites);
 }
 
 void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st)
 {
     long long g = (total_sites + 255) / 256;
-    if (g > 152LL * 16) g = 152LL * 16;
+    if (g > 152LL * 8) g = 152LL * 8;
     k_metal_batch<<<(unsigned)g, 256, 0, st>>>(a);
 }
 
