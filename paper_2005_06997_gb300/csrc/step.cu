@@ -113,7 +113,9 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
 // H_C^{n+1/2} at cell c from H^{n-1/2} = h0 and the E^n values of its curl
 // ((curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2}, (C, A1, A2) cyclic):
 // a_here, a_next = E_{A2} at idx and idx + e_A1, b_here, b_next = E_{A1} at idx
-// and idx + e_A2 (zero beyond the wall).  If own, store it and its psi.
+// and idx + e_A2 (zero beyond the wall).  psA1, psA2: psi_H^{n-1/2} of the
+// two derivatives (used only inside the slab of that axis).  If own, store it
+// and its psi.
 //
 // TF: the incident plane wave (E_x, H_y along +z) is converted where an H
 // read crosses the TF surface: H_y on the planes k = lo_z - 1 and k = hi_z
@@ -121,7 +123,7 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
 // E_x neighbour on the other side is a total field.
 template <int C, bool PML, bool TF>
 __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, float h0, float a_here, float a_next,
-                                        float b_here, float b_next, bool own)
+                                        float b_here, float b_next, bool own, float psA1 = 0.f, float psA2 = 0.f)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     if (TF) {
@@ -139,14 +141,12 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
     if (PML) {
         const int ix[3] = {c.i, c.j, c.k};
         if (c.l[A1] >= 0) {
-            const float psi = __ldg(p.bH[A1] + ix[A1]) * __ldg(p.psiH0[A1][1] + c.s[A1]) +
-                              __ldg(p.cH[A1] + ix[A1]) * t1;
+            const float psi = __ldg(p.bH[A1] + ix[A1]) * psA1 + __ldg(p.cH[A1] + ix[A1]) * t1;
             if (own) p.psiH1[A1][1][c.s[A1]] = psi;
             t1 += psi;
         }
         if (c.l[A2] >= 0) {
-            const float psi = __ldg(p.bH[A2] + ix[A2]) * __ldg(p.psiH0[A2][0] + c.s[A2]) +
-                              __ldg(p.cH[A2] + ix[A2]) * t2;
+            const float psi = __ldg(p.bH[A2] + ix[A2]) * psA2 + __ldg(p.cH[A2] + ix[A2]) * t2;
             if (own) p.psiH1[A2][0][c.s[A2]] = psi;
             t2 += psi;
         }
@@ -157,13 +157,14 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
 }
 
 // E_C^{n+1} of the background at cell c from E^n = En and H^{n+1/2}:
-// hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2).
+// hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2);
+// peA1, peA2: psi_E^n of the two derivatives (used only inside the slab).
 // TF: E_x on the planes k = lo_z and k = hi_z, and E_z on the planes
 // i = lo_x and i = hi_x, are total fields reading a scattered H_y.
 // Sites that hold a material are rewritten afterwards by k_metal.
 template <int C, bool PML, bool TF>
 __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float En, float hA2, float hA2m, float hA1,
-                                       float hA1m)
+                                       float hA1m, float peA1 = 0.f, float peA2 = 0.f)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     if (TF) {
@@ -181,12 +182,12 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float
     if (PML) {
         const int ix[3] = {c.i, c.j, c.k};
         if (c.l[A1] >= 0) {
-            const float psi = __ldg(p.bE[A1] + ix[A1]) * p.psiE[A1][1][c.s[A1]] + __ldg(p.cE[A1] + ix[A1]) * t1;
+            const float psi = __ldg(p.bE[A1] + ix[A1]) * peA1 + __ldg(p.cE[A1] + ix[A1]) * t1;
             p.psiE[A1][1][c.s[A1]] = psi;
             t1 += psi;
         }
         if (c.l[A2] >= 0) {
-            const float psi = __ldg(p.bE[A2] + ix[A2]) * p.psiE[A2][0][c.s[A2]] + __ldg(p.cE[A2] + ix[A2]) * t2;
+            const float psi = __ldg(p.bE[A2] + ix[A2]) * peA2 + __ldg(p.cE[A2] + ix[A2]) * t2;
             p.psiE[A2][0][c.s[A2]] = psi;
             t2 += psi;
         }
@@ -425,10 +426,90 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
 // block barrier: the store of plane k+2 goes to the buffer of plane k-1, read
 // last before the previous barrier, and the H plane of k+1 goes to the buffer
 // read last by the E update of k-1.
+// CPML tiles stage the psi values of plane k+1 in shared memory with
+// asynchronous copies issued during plane k, so the slab's extra operands
+// arrive off the critical path.  Per thread (own cell), by component C:
+// slot 2C / 2C+1 = psi_H^{n-1/2} of the A1 / A2 derivative, 6+2C / 7+2C the
+// same for psi_E^n; per halo thread, its two H components' A1 / A2 psi_H.
+struct PsiShared {
+    float own[2][12][BX * BY];
+    float halo[2][4][BX + BY];
+};
+
 struct TileShared {
     float sE[3][3][BY + 2][BX + 2];
     float sH[2][3][BY + 1][BX + 1];
+    PsiShared ps;
 };
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Queue the psi operands of component C at cell c: psi_H (d1, d2) and, if
+// dE, psi_E (e1, e2), for the derivatives whose slab holds the cell.
+template <int C>
+__device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, float* d1, float* d2, float* e1,
+                                          float* e2)
+{
+    constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
+    if (c.l[A1] >= 0) {
+        cp_async4(d1, p.psiH0[A1][1] + c.s[A1]);
+        if (e1) cp_async4(e1, p.psiE[A1][1] + c.s[A1]);
+    }
+    if (c.l[A2] >= 0) {
+        cp_async4(d2, p.psiH0[A2][0] + c.s[A2]);
+        if (e2) cp_async4(e2, p.psiE[A2][0] + c.s[A2]);
+    }
+}
+
+// Queue every psi operand of plane kk into buffer b: own cell (i, j, kk) and,
+// for the halo threads, their halo H cell.
+__device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, int b, int kk, int x0, int y0, int i,
+                                          int j, bool in, int slx, int sly, int tid)
+{
+    if (in) {
+        Cell c;
+        c.i = i;
+        c.j = j;
+        c.k = kk;
+        c.l[0] = slx;
+        c.l[1] = sly;
+        c.l[2] = slab_local(p, 2, kk);
+        if (c.l[0] >= 0 || c.l[1] >= 0 || c.l[2] >= 0) {
+            cell_slabs(p, c);
+            float(*o)[BX * BY] = ps.own[b];
+            psi_fetch<0>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
+            psi_fetch<1>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
+            psi_fetch<2>(p, c, &o[4][tid], &o[5][tid], &o[10][tid], &o[11][tid]);
+        }
+    }
+    float(*h)[BX + BY] = ps.halo[b];
+    if (tid < BY) {
+        const int jh = y0 + tid;
+        if (x0 > 0 && jh < p.ny) {
+            const Cell c = make_cell(p, x0 - 1, jh, kk, true);
+            psi_fetch<1>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
+            psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
+        }
+    } else if (tid < BY + BX) {
+        const int ih = x0 + tid - BY;
+        if (y0 > 0 && ih < p.nx) {
+            const Cell c = make_cell(p, ih, y0 - 1, kk, true);
+            psi_fetch<0>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
+            psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
+        }
+    }
+    cp_async_commit();
+}
 
 // Tile classes (uniform per block): PML = the tile or its halo reaches a
 // CPML slab; TF = it reaches the cells next to the TF/SF surface.  A tile of
@@ -458,24 +539,43 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         __syncthreads();
         if (in) {
             const Cell c = make_cell(p, i, j, k0 - 1, PML);
+            // psi_H of H_x (A1 = y, A2 = z) and H_y (A1 = z, A2 = x) at plane k0-1
+            float px1 = 0.f, px2 = 0.f, py1 = 0.f, py2 = 0.f;
+            if (PML) {
+                if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
+                if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
+                if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
+                if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
+            }
             hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), sE[fre][2][ly][lx], sE[fre][2][ly + 1][lx],
-                                         sE[fre][1][ly][lx], sE[cur][1][ly][lx], false);
+                                         sE[fre][1][ly][lx], sE[cur][1][ly][lx], false, px1, px2);
             hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), sE[fre][0][ly][lx], sE[cur][0][ly][lx],
-                                         sE[fre][2][ly][lx], sE[fre][2][ly][lx + 1], false);
+                                         sE[fre][2][ly][lx], sE[fre][2][ly][lx + 1], false, py1, py2);
         }
     }
     h_load(p, x0, y0, k0, i, j, in, tid, hr);
+    if (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
     __syncthreads();
-    int hb = 0;
+    int hb = 0, pb = 0;
     for (int k = k0; k < k1; ++k) {
         float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
         const bool more = k + 1 < k1;
-        // prefetch plane k+2 of E and plane k+1 of H^{n-1/2}
+        // prefetch plane k+2 of E and plane k+1 of H^{n-1/2} (and of psi)
         HRegs hn = hr;
         if (more) {
             plane_load(p, x0, y0, k + 2, tx, ty, tid, pr);
             h_load(p, x0, y0, k + 1, i, j, in, tid, hn);
         }
+        if (PML) {
+            if (more) {
+                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, slx, sly, tid);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+        }
+        const float* po = &sm.ps.own[pb][0][tid];
+        const float* ph = &sm.ps.halo[pb][0][tid < BY + BX ? tid : 0];
         Cell c;
         c.i = i;
         c.j = j;
@@ -492,9 +592,13 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             ex = sE[cur][0][ly][lx];
             ey = sE[cur][1][ly][lx];
             ez = sE[cur][2][ly][lx];
-            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nxt][1][ly][lx], true);
-            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nxt][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true);
-            hz = h_cell<2, PML, TF>(p, c, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true);
+            constexpr int S = BX * BY;
+            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nxt][1][ly][lx], true,
+                                    PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f);
+            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nxt][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true,
+                                    PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f);
+            hz = h_cell<2, PML, TF>(p, c, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true,
+                                    PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f);
             sH[0][ly][lx] = hx;
             sH[1][ly][lx] = hy;
             sH[2][ly][lx] = hz;
@@ -504,19 +608,25 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             const int jh = y0 + tid, sy = tid + 1;
             if (x0 > 0 && jh < p.ny) {
                 const Cell h = make_cell(p, x0 - 1, jh, k, PML);
+                constexpr int S = BX + BY;
                 sH[1][sy][0] = h_cell<1, PML, TF>(p, h, hr.halo[0], sE[cur][0][sy][0], sE[nxt][0][sy][0],
-                                                  sE[cur][2][sy][0], sE[cur][2][sy][1], false);
+                                                  sE[cur][2][sy][0], sE[cur][2][sy][1], false,
+                                                  PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
                 sH[2][sy][0] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
-                                                  sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false);
+                                                  sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false,
+                                                  PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
             }
         } else if (tid < BY + BX) {
             const int ih = x0 + tid - BY, sx = tid - BY + 1;
             if (y0 > 0 && ih < p.nx) {
                 const Cell h = make_cell(p, ih, y0 - 1, k, PML);
+                constexpr int S = BX + BY;
                 sH[0][0][sx] = h_cell<0, PML, TF>(p, h, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
-                                                  sE[cur][1][0][sx], sE[nxt][1][0][sx], false);
+                                                  sE[cur][1][0][sx], sE[nxt][1][0][sx], false,
+                                                  PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
                 sH[2][0][sx] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
-                                                  sE[cur][0][0][sx], sE[cur][0][1][sx], false);
+                                                  sE[cur][0][0][sx], sE[cur][0][1][sx], false,
+                                                  PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
             }
         }
         if (more) plane_store(sE[fre], pr, x0, y0, tx, ty, tid);
@@ -526,16 +636,17 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
             const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
             if (PML || TF) {
+                constexpr int S = BX * BY;
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev);
+                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi);
+                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm);
+                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -553,6 +664,7 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         nxt = fre;
         fre = t;
         hb ^= 1;
+        pb ^= 1;
     }
 }
 
