@@ -151,10 +151,14 @@ typedef struct {
     long long bbox_cells;         /* cells of the metal bounding box (with margin) */
     long long pml_slab_cells;     /* sum over CPML axes of slab cells */
     long long dft_records;        /* flux-face samples (without the incident record) */
-    double step_bytes;            /* algorithmic HBM bytes of one time step: 48 cells
-                                   * + 8 (2 + gnor + 2 n_poles) metal_sites + 32 pml_slab_cells
-                                   * + 3 bbox_cells (E and H read and written once, the
-                                   * hydrodynamic state, the CPML psi, the material ids) */
+    double step_bytes;            /* algorithmic HBM bytes of one time step, the sum of the two below */
+    double step_kernel_bytes;     /* EM step kernel: 48 cells + 32 pml_slab_cells (E and H read
+                                   * and written once, per slab cell and axis two psi_E read and
+                                   * written, two psi_H read and written) */
+    double metal_kernel_bytes;    /* material update: 17 material_sites (site entry 4, id 1, E read
+                                   * and written 8, H 4) + 8 (2 + gnor) metal_sites (P_f, a_f and
+                                   * the GNOR history read and written) + 16 n_poles pole_sites */
+    long long material_sites;     /* E-sites holding any material (entries of the site list) */
     double dt;                    /* s */
     int gnor, n_poles;
     long long h2d_bytes;          /* bytes copied host -> device by this context so far */
@@ -285,6 +289,14 @@ int nlf_flux_spectra_static(const double* acc_e, const double* acc_h, const doub
  * context has launched (graph replays count each kernel node). */
 long long nlf_time_index(const nlf_ctx* ctx);
 int nlf_get_info(nlf_ctx* ctx, nlf_info* info);
+
+/* Measurement: advance `steps` time steps one launch at a time (no graph),
+ * with CUDA events recorded on cuda_stream around each kernel, then wait for
+ * them and return the summed device durations in ms: ms_out[0] EM step
+ * kernel, ms_out[1] material update, ms_out[2] running-DFT kernels.  The
+ * solution advances exactly as with nlf_run.  The paper has no counterpart.
+ * Errors: NLF_E_ARG (steps < 1 or > 65536, null ms_out), NLF_E_CUDA. */
+int nlf_time_kernels(nlf_ctx* ctx, long long steps, void* cuda_stream, double* ms_out);
 long long nlf_kernel_launches(const nlf_ctx* ctx);
 
 const char* nlf_last_error(const nlf_ctx* ctx);

@@ -669,8 +669,11 @@ int initialise(nlf_ctx* c, cudaStream_t st)
     in.dt = c->dt;
     in.gnor = c->any_gnor;
     in.n_poles = c->max_poles;
-    in.step_bytes = 48.0 * c->ncell + 8.0 * (2 + (c->any_gnor ? 1 : 0) + 2 * c->max_poles) * in.metal_sites +
-                    32.0 * in.pml_slab_cells + 3.0 * c->nbb;
+    in.material_sites = c->n_msites;
+    in.step_kernel_bytes = 48.0 * c->ncell + 32.0 * in.pml_slab_cells;
+    in.metal_kernel_bytes = 17.0 * c->n_msites + 8.0 * (2 + (c->any_gnor ? 1 : 0)) * in.metal_sites +
+                            16.0 * c->max_poles * in.pole_sites;
+    in.step_bytes = in.step_kernel_bytes + in.metal_kernel_bytes;
     c->ready = true;
     return NLF_OK;
 }
@@ -694,6 +697,8 @@ int ensure_ready(nlf_ctx* c, cudaStream_t st)
     return initialise(c, st);
 }
 
+void monitor_work(nlf_ctx* c, cudaStream_t st);
+
 // One time step and its monitor work, launched on st.
 void step_once(nlf_ctx* c, cudaStream_t st)
 {
@@ -704,6 +709,12 @@ void step_once(nlf_ctx* c, cudaStream_t st)
         c->launches += 1;
     }
     c->n += 1;
+    monitor_work(c, st);
+}
+
+// The running-DFT work due after time step n (c->n already advanced).
+void monitor_work(nlf_ctx* c, cudaStream_t st)
+{
     if (c->have_mon && c->n % c->K == 0) {
         const int cur = (int)(c->n & 1);
         Header* h = at<Header>(c, c->off_hdr);
@@ -1177,6 +1188,58 @@ int nlf_run(nlf_ctx* c, long long steps, void* stream)
         }
     }
     CK(cudaGetLastError());
+    CK(cudaEventRecord(c->done, st));
+    return NLF_OK;
+}
+
+int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
+{
+    if (!c || !ms_out || steps < 1 || steps > 65536) return NLF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_ready(c, st);
+    if (rc) return rc;
+    c->stream = st;
+    // four events per step: before the step kernel, after it, after the
+    // material update, after the monitor kernels
+    std::vector<cudaEvent_t> ev((size_t)(4 * steps), nullptr);
+    auto release = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            release();
+            return fail(c, NLF_E_CUDA, "event creation failed");
+        }
+    for (long long s = 0; s < steps; ++s) {
+        cudaEvent_t* e = &ev[(size_t)(4 * s)];
+        cudaEventRecord(e[0], st);
+        nlf::launch_step(c->sp[c->n & 1], st);
+        c->launches += 1;
+        cudaEventRecord(e[1], st);
+        if (c->n_msites > 0) {
+            nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
+            c->launches += 1;
+        }
+        cudaEventRecord(e[2], st);
+        c->n += 1;
+        monitor_work(c, st);
+        cudaEventRecord(e[3], st);
+    }
+    cudaError_t err = cudaEventSynchronize(ev.back());
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long s = 0; s < steps && err == cudaSuccess; ++s) {
+        cudaEvent_t* e = &ev[(size_t)(4 * s)];
+        for (int q = 0; q < 3; ++q) {
+            float ms = 0.f;
+            err = cudaEventElapsedTime(&ms, e[q], e[q + 1]);
+            if (err != cudaSuccess) break;
+            acc[q] += ms;
+        }
+    }
+    release();
+    if (err != cudaSuccess) return fail(c, NLF_E_CUDA, "kernel timing: %s", cudaGetErrorString(err));
+    for (int q = 0; q < 3; ++q) ms_out[q] = acc[q];
     CK(cudaEventRecord(c->done, st));
     return NLF_OK;
 }

@@ -59,7 +59,8 @@ class nlf_monitors(C.Structure):
 class nlf_info(C.Structure):
     _fields_ = [("cells", C.c_longlong), ("metal_sites", C.c_longlong), ("pole_sites", C.c_longlong),
                 ("bbox_cells", C.c_longlong), ("pml_slab_cells", C.c_longlong), ("dft_records", C.c_longlong),
-                ("step_bytes", C.c_double), ("dt", C.c_double), ("gnor", C.c_int), ("n_poles", C.c_int),
+                ("step_bytes", C.c_double), ("step_kernel_bytes", C.c_double), ("metal_kernel_bytes", C.c_double),
+                ("material_sites", C.c_longlong), ("dt", C.c_double), ("gnor", C.c_int), ("n_poles", C.c_int),
                 ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong)]
 
 
@@ -89,6 +90,7 @@ SIGNATURES = {
     "nlf_flux_spectra_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int,
                                           C.c_double, C.c_void_p, C.c_void_p]),
     "nlf_time_index": (C.c_longlong, [_P]),
+    "nlf_time_kernels": (C.c_int, [_P, C.c_longlong, C.c_void_p, C.POINTER(C.c_double)]),
     "nlf_get_info": (C.c_int, [_P, C.POINTER(nlf_info)]),
     "nlf_kernel_launches": (C.c_longlong, [_P]),
     "nlf_last_error": (C.c_char_p, [_P]),
@@ -263,6 +265,14 @@ class Solver:
     def run(self, steps: int, stream=None):
         s = C.c_void_p(int(stream) if stream is not None else 0)
         _check(self.h, self.L.nlf_run(self.h, int(steps), s))
+
+    def time_kernels(self, steps: int, stream=None) -> dict:
+        """Advance `steps` steps one launch at a time with CUDA events around
+        each kernel; summed device ms per kernel class."""
+        s = C.c_void_p(int(stream) if stream is not None else 0)
+        ms = (C.c_double * 3)()
+        _check(self.h, self.L.nlf_time_kernels(self.h, int(steps), s, ms))
+        return {"step_ms": ms[0], "metal_ms": ms[1], "dft_ms": ms[2]}
 
     def reset(self, stream=None):
         s = C.c_void_p(int(stream) if stream is not None else 0)
