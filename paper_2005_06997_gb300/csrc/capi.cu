@@ -25,6 +25,8 @@
 
 namespace nlf {
 void launch_step(const StepParams& p, cudaStream_t st);
+void launch_step_pml(const StepParams& p, cudaStream_t st);
+bool step_has_pml(const StepParams& p);
 void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
 void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
@@ -107,6 +109,8 @@ struct nlf_ctx {
     cudaStream_t stream = nullptr;      // stream of the last run
     cudaEvent_t done = nullptr;
     cudaStream_t cap = nullptr;         // private stream for graph capture
+    cudaStream_t aux = nullptr;         // second stream of the step: the CPML tiles
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     long long n = 0;                    // time index
@@ -694,16 +698,38 @@ int ensure_ready(nlf_ctx* c, cudaStream_t st)
         c->owned = true;
     }
     if (!c->done) CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+    if (!c->aux) CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    if (!c->join) CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
     return initialise(c, st);
 }
 
 void monitor_work(nlf_ctx* c, cudaStream_t st);
 
+// The EM step of time step n on st: with CPML tiles, their kernel runs on the
+// context's second stream concurrently with the other tiles' kernel, forked
+// from and joined back into st (a fork / join inside a captured graph too).
+void launch_em(nlf_ctx* c, cudaStream_t st)
+{
+    const nlf::StepParams& sp = c->sp[c->n & 1];
+    if (nlf::step_has_pml(sp)) {
+        cudaEventRecord(c->fork, st);
+        cudaStreamWaitEvent(c->aux, c->fork, 0);
+        nlf::launch_step_pml(sp, c->aux);
+        nlf::launch_step(sp, st);
+        cudaEventRecord(c->join, c->aux);
+        cudaStreamWaitEvent(st, c->join, 0);
+        c->launches += 2;
+    } else {
+        nlf::launch_step(sp, st);
+        c->launches += 1;
+    }
+}
+
 // One time step and its monitor work, launched on st.
 void step_once(nlf_ctx* c, cudaStream_t st)
 {
-    nlf::launch_step(c->sp[c->n & 1], st);
-    c->launches += 1;
+    launch_em(c, st);
     if (c->n_msites > 0) {
         nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
         c->launches += 1;
@@ -1214,8 +1240,7 @@ int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
     for (long long s = 0; s < steps; ++s) {
         cudaEvent_t* e = &ev[(size_t)(4 * s)];
         cudaEventRecord(e[0], st);
-        nlf::launch_step(c->sp[c->n & 1], st);
-        c->launches += 1;
+        launch_em(c, st);
         cudaEventRecord(e[1], st);
         if (c->n_msites > 0) {
             nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
@@ -1507,6 +1532,9 @@ void nlf_destroy(nlf_ctx* c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->done) cudaEventDestroy(c->done);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     if (c->owned && c->base) cudaFree(c->base);
     delete c;
 }

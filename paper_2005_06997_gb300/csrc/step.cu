@@ -436,6 +436,11 @@ struct PsiShared {
     float halo[2][4][BX + BY];
 };
 
+struct TileSharedBG {
+    float sE[3][3][BY + 2][BX + 2];
+    float sH[2][3][BY + 1][BX + 1];
+};
+
 struct TileShared {
     float sE[3][3][BY + 2][BX + 2];
     float sH[2][3][BY + 1][BX + 1];
@@ -514,8 +519,8 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
 // Tile classes (uniform per block): PML = the tile or its halo reaches a
 // CPML slab; TF = it reaches the cells next to the TF/SF surface.  A tile of
 // neither class runs plain Yee arithmetic with no per-cell test.
-template <bool PML, bool TF>
-__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, TileShared& sm)
+template <bool PML, bool TF, class SM>
+__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
 {
     float (*sE)[3][BY + 2][BX + 2] = sm.sE;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -554,7 +559,7 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         }
     }
     h_load(p, x0, y0, k0, i, j, in, tid, hr);
-    if (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
+    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
     __syncthreads();
     int hb = 0, pb = 0;
     for (int k = k0; k < k1; ++k) {
@@ -566,16 +571,18 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
             plane_load(p, x0, y0, k + 2, tx, ty, tid, pr);
             h_load(p, x0, y0, k + 1, i, j, in, tid, hn);
         }
-        if (PML) {
+        const float* po = nullptr;
+        const float* ph = nullptr;
+        if constexpr (PML) {
             if (more) {
                 psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, slx, sly, tid);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
+            po = &sm.ps.own[pb][0][tid];
+            ph = &sm.ps.halo[pb][0][tid < BY + BX ? tid : 0];
         }
-        const float* po = &sm.ps.own[pb][0][tid];
-        const float* ph = &sm.ps.halo[pb][0][tid < BY + BX ? tid : 0];
         Cell c;
         c.i = i;
         c.j = j;
@@ -718,10 +725,45 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, i
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(BX * BY, 4) k_step(const StepParams p, int kz)
+// The single-grid step runs as two kernels over the same grid of tiles,
+// launched concurrently on two streams: k_step_pml takes the CPML tiles,
+// k_step the others (background and TF/SF), each block leaving at once if
+// its tile belongs to the other kernel.  Without CPML tiles k_step alone runs.
+// Separate kernels let the background tiles run with fewer registers and
+// without the psi staging area: 5 blocks per SM instead of 4.
+template <bool PMLK, class SM>
+__device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm)
+{
+    const int x0 = bx * BX, y0 = by * BY;
+    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
+    const int hi[3] = {x0 + BX, y0 + BY, k1};
+    bool pml, tf;
+    tile_class(p, lo, hi, &pml, &tf);
+    if (pml == PMLK) {
+        if (tf)
+            march<PMLK, true>(p, x0, y0, k0, k1, sm);
+        else
+            march<PMLK, false>(p, x0, y0, k0, k1, sm);
+    }
+    // the 1D incident grid and the step counter: block (0,0,0) of k_step
+    if (!PMLK && bx == 0 && by == 0 && bz == 0) {
+        const int tid = threadIdx.y * BX + threadIdx.x;
+        if (p.tfsf) inc_step(p, tid, BX * BY);
+        if (tid == 0) *p.step1 = *p.step0 + 1;
+    }
+}
+
+__global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
+{
+    __shared__ TileSharedBG sm;
+    step_tile_of<false>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
+}
+
+__global__ void __launch_bounds__(BX * BY, 4) k_step_pml(const StepParams p, int kz)
 {
     __shared__ TileShared sm;
-    step_tile(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
+    step_tile_of<true>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
 }
 
 // ---------------------------------------------------------------- batched
@@ -831,12 +873,22 @@ int step_kz(const StepParams& p)
     return kz;
 }
 
+bool step_has_pml(const StepParams& p) { return p.cpml[0] || p.cpml[1] || p.cpml[2]; }
+
 void launch_step(const StepParams& p, cudaStream_t st)
 {
     const int kz = step_kz(p);
     dim3 blk(BX, BY, 1);
     dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
     k_step<<<grd, blk, 0, st>>>(p, kz);
+}
+
+void launch_step_pml(const StepParams& p, cudaStream_t st)
+{
+    const int kz = step_kz(p);
+    dim3 blk(BX, BY, 1);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
+    k_step_pml<<<grd, blk, 0, st>>>(p, kz);
 }
 
 }  // namespace nlf
