@@ -218,8 +218,10 @@ int nlf_run(nlf_ctx* ctx, long long steps, void* cuda_stream);
 int nlf_reset(nlf_ctx* ctx, void* cuda_stream);
 
 /* Wait for the work queued by nlf_run, polling for at most timeout_ms
- * (< 0: no limit).  Checks the device error word and the non-finite
- * watchdog.  Errors: NLF_E_TIMEOUT (work still running; nothing is lost),
+ * (< 0: no limit).  Checks the device error word: the non-finite watchdog
+ * (NLF_E_UNSTABLE) and the step kernel's bounded waits for its tensor-memory
+ * copies (NLF_E_CUDA if one gave up; the kernel then skipped the rest of that
+ * tile).  Errors: NLF_E_TIMEOUT (work still running; nothing is lost),
  * NLF_E_UNSTABLE, NLF_E_CUDA. */
 int nlf_sync(nlf_ctx* ctx, int timeout_ms);
 

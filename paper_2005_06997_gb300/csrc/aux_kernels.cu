@@ -263,15 +263,22 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
 
 namespace nlf {
 
-__global__ void k_field_out(const float* __restrict__ src, float* __restrict__ dst, long long n, float scale)
+// Copy one field component out of the padded layout (rows of px floats, nx
+// used) into a dense [nz][ny][nx] array, scaled.
+__global__ void k_field_out(const float* __restrict__ src, float* __restrict__ dst, int nx, int px, long long n,
+                            float scale)
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) dst[q] = src[q] * scale;
+    if (q >= n) return;
+    const long long row = q / nx;
+    const int i = (int)(q - row * nx);
+    dst[q] = src[row * px + i] * scale;
 }
 
-void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st)
+void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st)
 {
-    k_field_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, scale);
+    const long long n = rows * nx;
+    k_field_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, nx, px, n, scale);
 }
 
 }  // namespace nlf

@@ -5,6 +5,8 @@
 // the device.  Time steps are launched eagerly or replayed from a CUDA graph
 // that holds a whole DFT period (K * B steps): the step kernel, the sample
 // gathers and the accumulation.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,7 +37,7 @@ void launch_dft_gather(const DftParams& d, const float* E, const float* H, const
 void launch_dft_flush(const DftParams& d, int count, cudaStream_t st);
 void launch_flux(const double2* accE, const double2* accH, const double* coef, long long n_abs, long long nrec,
                  int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
-void launch_field_out(const float* src, float* dst, long long n, float scale, cudaStream_t st);
+void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st);
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st);
@@ -64,6 +66,10 @@ struct nlf_ctx {
     nlf_grid g{};
     double dt = 0, c0 = 0, eta0 = 0;
     long long ncell = 0;
+    int px = 0;                     // row pitch of the field arrays: nx rounded up to 8 (32-byte rows)
+    CUtensorMap tmaps[4];           // E gen 0, E gen 1, H gen 0, H gen 1 (host copy of the device tables)
+    size_t off_tmap = 0;
+    long long nfield = 0;           // floats per field component: px ny nz
     std::vector<nlf_material> mats;
     std::vector<nlf_shape> shapes;
     std::vector<uint8_t> map;      // full [3][nz][ny][nx] map if given
@@ -232,7 +238,7 @@ nlf::MatCoef make_coef(const nlf_ctx* c, const nlf_material& m)
 void box_records(const nlf_ctx* c, const int lo[3], const int hi[3], std::vector<uint32_t>& re,
                  std::vector<uint32_t>& rh, std::vector<uint32_t>& rs, std::vector<double>& co)
 {
-    const long long st[3] = {1, c->g.nx, (long long)c->g.nx * c->g.ny};
+    const long long st[3] = {1, c->px, (long long)c->px * c->g.ny};
     for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, cc = (a + 2) % 3;
         const int slow = std::max(b, cc), fast = std::min(b, cc);
@@ -254,8 +260,8 @@ void box_records(const nlf_ctx* c, const int lo[3], const int hi[3], std::vector
                         idx[fast] = tf;
                         const double w = (idx[other] == lo[other] || idx[other] == hi[other]) ? 0.5 : 1.0;
                         const long long cell = idx[0] * st[0] + idx[1] * st[1] + idx[2] * st[2];
-                        re.push_back((uint32_t)(ec * c->ncell + cell));
-                        rh.push_back((uint32_t)(hc * c->ncell + cell - st[a]));
+                        re.push_back((uint32_t)(ec * c->nfield + cell));
+                        rh.push_back((uint32_t)(hc * c->nfield + cell - st[a]));
                         rs.push_back((uint32_t)st[a]);
                         co.push_back(outward * tsign * w * 0.5);
                     }
@@ -382,8 +388,9 @@ int plan(nlf_ctx* c)
         o = align_up(o + nbytes, 256);
         return r;
     };
-    const size_t f3 = 3 * (size_t)c->ncell * sizeof(float);
+    const size_t f3 = 3 * (size_t)c->nfield * sizeof(float);
     c->off_hdr = take(sizeof(Header));
+    c->off_tmap = take(4 * sizeof(CUtensorMap));
     for (int gI = 0; gI < 2; ++gI) c->off_E[gI] = take(f3);
     for (int gI = 0; gI < 2; ++gI) c->off_H[gI] = take(f3);
     for (int a = 0; a < 3; ++a) {
@@ -429,6 +436,39 @@ int plan(nlf_ctx* c)
     return NLF_OK;
 }
 
+// Tensor maps of the four field arrays for the TMA-fed step kernel: 4D
+// [3][nz][ny][px] floats, globally nx x ny x nz x 3 (cells past nx, below 0
+// or past the grid read as zero), boxes of NLF_TMA_BOX_X x (EY | HY) x 1 x 3.
+int encode_maps(nlf_ctx* c)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+                return fail(c, NLF_E_CUDA, "cuTensorMapEncodeTiled not available");
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)c->g.nx, (cuuint64_t)c->g.ny, (cuuint64_t)c->g.nz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)c->px * 4, (cuuint64_t)c->px * c->g.ny * 4, (cuuint64_t)c->nfield * 4};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    for (int m = 0; m < 4; ++m) {
+        const bool isE = m < 2;
+        const cuuint32_t box[4] = {NLF_TMA_BOX_X, isE ? NLF_TMA_BOX_EY : NLF_TMA_BOX_HY, 1, 3};
+        void* base = c->base + (isE ? c->off_E[m & 1] : c->off_H[m & 1]);
+        CUresult r = encode(&c->tmaps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(c, NLF_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return NLF_OK;
+}
+
 void fill_params(nlf_ctx* c)
 {
     const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
@@ -437,15 +477,18 @@ void fill_params(nlf_ctx* c)
         memset(&p, 0, sizeof p);
         const int r = par, w = 1 - par;
         p.nx = c->g.nx;
+        p.px = c->px;
+        p.tmE = c->base + c->off_tmap + (size_t)r * sizeof(CUtensorMap);
+        p.tmH = c->base + c->off_tmap + (size_t)(2 + r) * sizeof(CUtensorMap);
         p.ny = c->g.ny;
         p.nz = c->g.nz;
         p.S = (float)c->g.courant;
         p.Sb = (float)(c->g.courant / c->g.eps_background);
         for (int k = 0; k < 3; ++k) {
-            p.E0[k] = at<float>(c, c->off_E[r]) + k * c->ncell;
-            p.H0[k] = at<float>(c, c->off_H[r]) + k * c->ncell;
-            p.E1[k] = at<float>(c, c->off_E[w]) + k * c->ncell;
-            p.H1[k] = at<float>(c, c->off_H[w]) + k * c->ncell;
+            p.E0[k] = at<float>(c, c->off_E[r]) + k * c->nfield;
+            p.H0[k] = at<float>(c, c->off_H[r]) + k * c->nfield;
+            p.E1[k] = at<float>(c, c->off_E[w]) + k * c->nfield;
+            p.H1[k] = at<float>(c, c->off_H[w]) + k * c->nfield;
         }
         p.pml = c->g.pml_cells;
         for (int a = 0; a < 3; ++a) {
@@ -554,6 +597,8 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         return NLF_OK;
     };
     int rc;
+    if ((rc = encode_maps(c))) return rc;
+    if ((rc = put(c->off_tmap, c->tmaps, sizeof c->tmaps))) return rc;
     for (int a = 0; a < 3; ++a) {
         std::vector<float> pr(4 * (size_t)n3[a], 0.f);
         for (int v = 0; v < n3[a]; ++v) {
@@ -1073,7 +1118,7 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out)
     const nlf_grid& g = *grid;
     if (g.nx < 8 || g.ny < 8 || g.nz < 8 || !(g.dx > 0.0) || !(g.courant > 0.0) || !(g.eps_background >= 1.0 - 1e-12))
         return NLF_E_ARG;
-    if ((long long)g.nx * g.ny * g.nz * 3 >= (1LL << 32)) return NLF_E_ARG;
+    if ((long long)((g.nx + 7) & ~7) * g.ny * g.nz * 3 >= (1LL << 32)) return NLF_E_ARG;
     if (g.courant > 1.0 / std::sqrt(3.0) + 1e-12) return NLF_E_CFL;
     for (int a = 0; a < 3; ++a) {
         if (g.boundary[a] == NLF_BC_PERIODIC) return NLF_E_UNSUPPORTED;
@@ -1087,6 +1132,8 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out)
     c->eta0 = std::sqrt(kMu0 / kEps0);
     c->dt = g.courant * g.dx / c->c0;
     c->ncell = (long long)g.nx * g.ny * g.nz;
+    c->px = (g.nx + 7) & ~7;
+    c->nfield = (long long)c->px * g.ny * g.nz;
     *out = c;
     return NLF_OK;
 }
@@ -1298,6 +1345,7 @@ int nlf_sync(nlf_ctx* c, int timeout_ms)
     int err = 0;
     CK(cudaMemcpy(&err, c->base + c->off_hdr + offsetof(Header, err), sizeof err, cudaMemcpyDeviceToHost));
     if (err & 1) return fail(c, NLF_E_UNSTABLE, "non-finite field sample at time index %lld", c->n);
+    if (err & 4) return fail(c, NLF_E_CUDA, "a tensor-memory copy of the step kernel did not complete in time");
     return NLF_OK;
 }
 
@@ -1311,15 +1359,18 @@ int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
     const int comp = which % 3;
     const size_t n = (size_t)c->ncell;
     if (which <= NLF_FIELD_HZ) {
-        const float* src = at<float>(c, which < 3 ? c->off_E[cur] : c->off_H[cur]) + comp * n;
+        const float* src = at<float>(c, which < 3 ? c->off_E[cur] : c->off_H[cur]) + comp * (size_t)c->nfield;
         const float scale = which < 3 ? 1.f : (float)(1.0 / c->eta0);
+        const long long rows = (long long)c->g.ny * c->g.nz;
         if (on_device) {
-            nlf::launch_field_out(src, (float*)dst, (long long)n, scale, st);
+            nlf::launch_field_out(src, (float*)dst, c->g.nx, c->px, rows, scale, st);
             c->launches += 1;
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(st));
         } else {
-            CK(cudaMemcpy(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost));
+            // drop the row padding: nx floats of every px-float row
+            CK(cudaMemcpy2D(dst, (size_t)c->g.nx * sizeof(float), src, (size_t)c->px * sizeof(float),
+                            (size_t)c->g.nx * sizeof(float), (size_t)rows, cudaMemcpyDeviceToHost));
             c->d2h += (long long)(n * sizeof(float));
             if (scale != 1.f)
                 for (size_t q = 0; q < n; ++q) ((float*)dst)[q] *= scale;
@@ -1432,6 +1483,8 @@ int nlf_load_state(nlf_ctx* c, const void* host)
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(c->base, host, c->bytes, cudaMemcpyHostToDevice));
+    // the tensor maps hold this buffer's addresses, not the saved state's
+    CK(cudaMemcpy(c->base + c->off_tmap, c->tmaps, sizeof c->tmaps, cudaMemcpyHostToDevice));
     Header h{};
     memcpy(&h, host, sizeof h);
     c->n = h.n;

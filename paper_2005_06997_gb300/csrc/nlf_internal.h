@@ -17,6 +17,12 @@
 #define NLF_MAX_POLES 4
 #endif
 #define NLF_MAX_MAT 32
+// TMA boxes of the background step kernel: x0-4 .. x0+35 along x, the tile's
+// 8 rows plus halo rows along y (E: y0-1 .. y0+8, H: y0-1 .. y0+7), one z
+// plane, three components
+#define NLF_TMA_BOX_X 40
+#define NLF_TMA_BOX_EY 10
+#define NLF_TMA_BOX_HY 9
 #define NLF_MAX_SHP 16
 #define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
 #define NLF_INC_MARGIN 10       // vacuum cells between the TF box and that CPML
@@ -50,6 +56,9 @@ struct Shape {
 // Everything the fused time step needs.  Pointers are device pointers.
 struct StepParams {
     int nx, ny, nz;
+    int px;             // row pitch of the field arrays (nx rounded up to 8): cell (i, j, k) at (k ny + j) px + i
+    const void* tmE;    // tensor maps (device memory, 64-byte aligned) of E^n and H^{n-1/2} as 4D
+    const void* tmH;    // [3][nz][ny][px] arrays, boxes of NLF_TMA_BOX_X x (EY | HY) x 1 x 3 floats
     float S;            // H curl coefficient
     float Sb;           // S / eps_b, background E curl coefficient
     const float* E0[3];

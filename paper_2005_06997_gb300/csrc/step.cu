@@ -1,20 +1,25 @@
-// step.cu -- one fused time step of the nonlocal hydrodynamic FDTD scheme.
+// step.cu -- one time step of the nonlocal hydrodynamic FDTD scheme.
 //
-// One launch advances (H^{n-1/2}, E^n, P^n) to (H^{n+1/2}, E^{n+1}, P^{n+1})
-// in the order of Sec. III: f1 (H), f2 (E), f3 (P_CP), f4 (P_f).  A thread
-// block owns a BX x BY column tile and marches through a chunk of z planes.
-// For plane k it stages E^n of planes k and k+1 (tile plus a one-cell halo)
-// in shared memory, computes H^{n+1/2} of the tile plus the -x / -y halo (the
-// halo H is the only recomputed work), keeps H of plane k-1 in registers,
-// and then updates E, P_CP and P_f of the tile.  The loads of plane k+2 and
-// of H^{n-1/2} of plane k+1 are issued into registers before plane k is
-// computed, so their latency overlaps the arithmetic.  E, H and psi_H are
-// double buffered (generation n read, n+1 written), so tiles need no
-// grid-wide barrier; every field crosses HBM once per step apart from halos.
+// Two kernels advance (H^{n-1/2}, E^n, P^n) to (H^{n+1/2}, E^{n+1}, P^{n+1})
+// in the order of Sec. III: f1 (H), f2 (E), f3 (P_CP), f4 (P_f).
 //
-// Tiles are classified once per block: tiles clear of the CPML slabs, of the
-// TF/SF surface and of the metal box run plain Yee arithmetic with no
-// per-cell tests; the others take the full path.
+// The EM step (k_step, k_step_pml, or k_step_batch over many grids): a
+// thread block owns a BX x BY column tile and marches through a chunk of z
+// planes.  For plane k it holds E^n of planes k and k+1 (tile plus a one-cell
+// halo) in shared memory, computes H^{n+1/2} of the tile plus the -x / -y
+// halo (the halo H is the only recomputed work), keeps H of plane k-1 in
+// registers, and then updates the background E of the tile.  Planes arrive
+// ahead of use: by TMA into a ring of shared-memory stages (background tiles)
+// or by register prefetch (CPML tiles, batched grids), the CPML psi operands
+// by cp.async.  E, H and psi_H are double buffered (generation n read, n+1
+// written), so tiles need no grid-wide barrier; every field crosses HBM once
+// per step apart from halos.  Tiles are classified once per block: clear of
+// the CPML slabs and of the TF/SF surface they run plain Yee arithmetic with
+// no per-cell tests.
+//
+// The material update (k_metal): one thread per material E-site of a
+// compact list rewrites E^{n+1} there from the H^{n+1/2} just written and
+// advances P_CP and P_f.
 //
 // f2/f3/f4 are applied in increment form, algebraically identical to the
 // paper's printed recurrences (Eq. NonlocalUpdate, Eq. GNORUpdate,
@@ -31,7 +36,7 @@
 // GD^n = grad(div P_f^n) is evaluated as the difference of node divergences,
 // which equals Eq. GradDiv term by term.
 //
-// Offsets are 32-bit: the library rejects grids with 3 nx ny nz >= 2^32.
+// Offsets are 32-bit: the library rejects grids with 3 px ny nz >= 2^32.
 #include <cuda_runtime.h>
 
 #include "nlf_internal.h"
@@ -39,6 +44,8 @@
 namespace nlf {
 
 constexpr int BX = 32, BY = 8;
+static_assert(NLF_TMA_BOX_X == BX + 8 && NLF_TMA_BOX_EY == BY + 2 && NLF_TMA_BOX_HY == BY + 1,
+              "tensor-map boxes must match the tile");
 
 // Half-cell offsets of the Yee positions (Table Yee).
 __device__ __forceinline__ int eoff(int c, int a) { return c == a ? 1 : 0; }
@@ -99,7 +106,7 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
     c.i = i;
     c.j = j;
     c.k = k;
-    c.q = ((uint32_t)k * p.ny + j) * p.nx + i;
+    c.q = ((uint32_t)k * p.ny + j) * p.px + i;
     c.l[0] = c.l[1] = c.l[2] = -1;
     if (pml) {
         c.l[0] = slab_local(p, 0, i);
@@ -215,7 +222,7 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b)
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
     const uint32_t bk = b / sz, r = b - bk * sz, bj = r / sy, bi = r - bj * sy;
-    const uint32_t st[3] = {1u, (uint32_t)p.nx, (uint32_t)p.nx * (uint32_t)p.ny};
+    const uint32_t st[3] = {1u, (uint32_t)p.px, (uint32_t)p.px * (uint32_t)p.ny};
     const uint32_t q = (uint32_t)(p.bb_lo[2] + (int)bk) * st[2] + (uint32_t)(p.bb_lo[1] + (int)bj) * st[1] +
                        (uint32_t)(p.bb_lo[0] + (int)bi);
     const int id = __ldg(p.mat[C] + b);
@@ -356,11 +363,11 @@ __device__ __forceinline__ void plane_load(const StepParams& p, int x0, int y0, 
                                            PlaneRegs& r)
 {
     const bool kin = kk >= 0 && kk < p.nz;
-    const uint32_t base = kin ? (uint32_t)kk * (uint32_t)p.ny * (uint32_t)p.nx : 0u;
+    const uint32_t base = kin ? (uint32_t)kk * (uint32_t)p.ny * (uint32_t)p.px : 0u;
     {
         const int gi = x0 + tx, gj = y0 + ty;
         const bool ok = kin && gi < p.nx && gj < p.ny;
-        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.nx + (ok ? gi : 0);
+        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.px + (ok ? gi : 0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) r.in[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
     }
@@ -368,7 +375,7 @@ __device__ __forceinline__ void plane_load(const StepParams& p, int x0, int y0, 
         int gi, gj, sx, sy;
         halo_cell(tid, x0, y0, &gi, &gj, &sx, &sy);
         const bool ok = kin && gi >= 0 && gi < p.nx && gj >= 0 && gj < p.ny;
-        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.nx + (ok ? gi : 0);
+        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.px + (ok ? gi : 0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) r.halo[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
     }
@@ -398,23 +405,23 @@ struct HRegs {
 __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int kk, int i, int j, bool in, int tid,
                                        HRegs& r)
 {
-    const uint32_t plane = (uint32_t)p.nx * (uint32_t)p.ny;
+    const uint32_t plane = (uint32_t)p.px * (uint32_t)p.ny;
     if (in) {
-        const uint32_t q = (uint32_t)kk * plane + (uint32_t)j * p.nx + i;
+        const uint32_t q = (uint32_t)kk * plane + (uint32_t)j * p.px + i;
 #pragma unroll
         for (int c = 0; c < 3; ++c) r.own[c] = __ldg(p.H0[c] + q);
     }
     if (tid < BY) {
         const int jh = y0 + tid;
         if (x0 > 0 && jh < p.ny) {
-            const uint32_t q = (uint32_t)kk * plane + (uint32_t)jh * p.nx + (x0 - 1);
+            const uint32_t q = (uint32_t)kk * plane + (uint32_t)jh * p.px + (x0 - 1);
             r.halo[0] = __ldg(p.H0[1] + q);
             r.halo[1] = __ldg(p.H0[2] + q);
         }
     } else if (tid < BY + BX) {
         const int ih = x0 + tid - BY;
         if (y0 > 0 && ih < p.nx) {
-            const uint32_t q = (uint32_t)kk * plane + (uint32_t)(y0 - 1) * p.nx + ih;
+            const uint32_t q = (uint32_t)kk * plane + (uint32_t)(y0 - 1) * p.px + ih;
             r.halo[0] = __ldg(p.H0[0] + q);
             r.halo[1] = __ldg(p.H0[2] + q);
         }
@@ -434,11 +441,6 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
 struct PsiShared {
     float own[2][12][BX * BY];
     float halo[2][4][BX + BY];
-};
-
-struct TileSharedBG {
-    float sE[3][3][BY + 2][BX + 2];
-    float sH[2][3][BY + 1][BX + 1];
 };
 
 struct TileShared {
@@ -587,7 +589,7 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
         c.i = i;
         c.j = j;
         c.k = k;
-        c.q = ((uint32_t)k * p.ny + j) * p.nx + i;
+        c.q = ((uint32_t)k * p.ny + j) * p.px + i;
         c.l[0] = slx;
         c.l[1] = sly;
         c.l[2] = PML ? slab_local(p, 2, k) : -1;
@@ -675,6 +677,266 @@ __device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k
     }
 }
 
+// ------------------------------------------------------- TMA-fed z march
+//
+// The background tiles (no CPML) take their E^n and H^{n-1/2} planes from
+// the tensor memory accelerator instead of per-thread loads: one thread
+// issues a 4D tiled copy per plane (all three components, the tile with its
+// halo, out-of-grid cells zero-filled) into a ring of shared-memory stages,
+// each with an mbarrier that completes when the bytes have landed.  E planes
+// k+2 and k+3 and H planes k+1 and k+2 are in flight while plane k is
+// computed; a stage is refilled right after the block barrier that ends its
+// last reader.  Boxes start at x0 - 4 so that the innermost coordinate stays
+// a multiple of 16 bytes.
+
+constexpr int TMA_EX = BX + 8;                 // 40 floats per row (x0-4 .. x0+35)
+constexpr int TMA_EY = BY + 2;                 // rows y0-1 .. y0+BY
+constexpr int TMA_HY = BY + 1;                 // rows y0-1 .. y0+BY-1
+constexpr int TMA_E_FLOATS = 3 * TMA_EY * TMA_EX;
+constexpr int TMA_H_FLOATS = 3 * TMA_HY * TMA_EX;
+constexpr int TMA_E_STAGE = (TMA_E_FLOATS * 4 + 127) / 128 * 32;   // floats, 128-byte multiple
+constexpr int TMA_H_STAGE = (TMA_H_FLOATS * 4 + 127) / 128 * 32;
+constexpr int NE_STAGE = 4, NH_STAGE = 3;
+constexpr long long TMA_SPIN = 1LL << 21;      // bounded mbarrier wait (~2 s at the hint below)
+
+struct TileSharedTMA {
+    alignas(128) float sE[NE_STAGE][TMA_E_STAGE];
+    alignas(128) float sHo[NH_STAGE][TMA_H_STAGE];
+    float sH[2][3][BY + 1][BX + 1];
+    unsigned long long barE[NE_STAGE];
+    unsigned long long barH[NH_STAGE];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Wait for phase `parity` of the barrier, giving up after TMA_SPIN tries
+// (false: the copy did not land in time).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (long long it = 0; it < TMA_SPIN; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, 1000;\n"
+            " selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// One plane (all three components) of a [3][nz][ny][px] field: box origin
+// (x, y, z, 0), completion on bar.
+__device__ __forceinline__ void tma_plane(float* dst, const void* map, int x, int y, int z, unsigned long long* bar,
+                                          unsigned bytes)
+{
+    mbar_expect(bar, bytes);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// The ring of one block's z march: issue (thread 0) and wait (every thread)
+// by plane index.  Thread 0 also records which stages hold a copy not yet
+// waited for, so that after a timed-out wait it can let the copies in flight
+// land before the block exits.
+struct TmaRing {
+    TileSharedTMA& sm;
+    const StepParams& p;
+    int k0, x0, y0;
+    unsigned pendE = 0, parE = 0, pendH = 0, parH = 0;
+    bool bad = false;
+    __device__ int eslot(int pl) const { return (pl - k0 + 1) & 3; }
+    __device__ unsigned epar(int pl) const { return (unsigned)(((pl - k0 + 1) >> 2) & 1); }
+    __device__ int hslot(int pl) const { return (pl - k0) % 3; }
+    __device__ unsigned hpar(int pl) const { return (unsigned)(((pl - k0) / 3) & 1); }
+    __device__ void issue_e(int pl)
+    {
+        const int q = eslot(pl);
+        tma_plane(sm.sE[q], p.tmE, x0 - 4, y0 - 1, pl, &sm.barE[q], TMA_E_FLOATS * 4);
+        pendE |= 1u << q;
+        parE = (parE & ~(1u << q)) | (epar(pl) << q);
+    }
+    __device__ void issue_h(int pl)
+    {
+        const int q = hslot(pl);
+        tma_plane(sm.sHo[q], p.tmH, x0 - 4, y0 - 1, pl, &sm.barH[q], TMA_H_FLOATS * 4);
+        pendH |= 1u << q;
+        parH = (parH & ~(1u << q)) | (hpar(pl) << q);
+    }
+    __device__ void wait_e(int pl)
+    {
+        if (bad) return;
+        if (mbar_wait(&sm.barE[eslot(pl)], epar(pl)))
+            pendE &= ~(1u << eslot(pl));
+        else
+            bad = true;
+    }
+    __device__ void wait_h(int pl)
+    {
+        if (bad) return;
+        if (mbar_wait(&sm.barH[hslot(pl)], hpar(pl)))
+            pendH &= ~(1u << hslot(pl));
+        else
+            bad = true;
+    }
+    __device__ float e(int pl, int c, int y, int x) const { return sm.sE[eslot(pl)][(c * TMA_EY + y) * TMA_EX + x]; }
+    __device__ float h(int pl, int c, int y, int x) const { return sm.sHo[hslot(pl)][(c * TMA_HY + y) * TMA_EX + x]; }
+    // thread 0, after a block-wide failure: wait (bounded) for what is in flight
+    __device__ void drain()
+    {
+        for (int q = 0; q < NE_STAGE; ++q)
+            if (pendE >> q & 1u) mbar_wait(&sm.barE[q], parE >> q & 1u);
+        for (int q = 0; q < NH_STAGE; ++q)
+            if (pendH >> q & 1u) mbar_wait(&sm.barH[q], parH >> q & 1u);
+    }
+};
+
+template <bool TF>
+__device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, TileSharedTMA& sm)
+{
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool in = i < p.nx && j < p.ny;
+    const int lx = tx + 4, ly = ty + 1;               // own cell in an E or H stage
+    TmaRing r{sm, p, k0, x0, y0};
+    if (tid == 0) {
+        for (int q = 0; q < NE_STAGE; ++q) mbar_init(&sm.barE[q]);
+        for (int q = 0; q < NH_STAGE; ++q) mbar_init(&sm.barH[q]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        // the tensor maps were written to device memory by a copy, not by this proxy
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmE) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmH) : "memory");
+    }
+    __syncthreads();
+    // E planes k0-1 .. k0+2 and H planes k0 .. k0+2 (E is needed up to plane k1, H up to k1-1)
+    if (tid == 0) {
+        for (int pl = k0 - 1; pl <= k0 + 2 && pl <= k1; ++pl) r.issue_e(pl);
+        for (int pl = k0; pl <= k0 + 2 && pl < k1; ++pl) r.issue_h(pl);
+    }
+    // H_x, H_y of plane k0-1 (own column) for the first E update
+    float hx_prev = 0.f, hy_prev = 0.f;
+    r.wait_e(k0 - 1);
+    r.wait_e(k0);
+    if (!r.bad && k0 > 0 && in) {
+        const Cell c = make_cell(p, i, j, k0 - 1, false);
+        const int pm = k0 - 1;
+        hx_prev = h_cell<0, false, TF>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
+                                       r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false);
+        hy_prev = h_cell<1, false, TF>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
+                                       r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false);
+    }
+    bool fail = __syncthreads_or(r.bad);
+    if (!fail && tid == 0 && k0 + 3 <= k1) r.issue_e(k0 + 3);
+    int hb = 0;
+    for (int k = k0; k < k1 && !fail; ++k) {
+        float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
+        r.wait_e(k + 1);
+        r.wait_h(k);
+        Cell c;
+        c.i = i;
+        c.j = j;
+        c.k = k;
+        c.q = ((uint32_t)k * p.ny + j) * p.px + i;
+        c.l[0] = c.l[1] = c.l[2] = -1;
+        float hx = 0.f, hy = 0.f, hz = 0.f;
+        float ex = 0.f, ey = 0.f, ez = 0.f;
+        // f1: own H^{n+1/2}
+        if (in && !r.bad) {
+            ex = r.e(k, 0, ly, lx);
+            ey = r.e(k, 1, ly, lx);
+            ez = r.e(k, 2, ly, lx);
+            hx = h_cell<0, false, TF>(p, c, r.h(k, 0, ly, lx), ez, r.e(k, 2, ly + 1, lx), ey, r.e(k + 1, 1, ly, lx),
+                                      true);
+            hy = h_cell<1, false, TF>(p, c, r.h(k, 1, ly, lx), ex, r.e(k + 1, 0, ly, lx), ez, r.e(k, 2, ly, lx + 1),
+                                      true);
+            hz = h_cell<2, false, TF>(p, c, r.h(k, 2, ly, lx), ey, r.e(k, 1, ly, lx + 1), ex, r.e(k, 0, ly + 1, lx),
+                                      true);
+            sH[0][ly][tx + 1] = hx;
+            sH[1][ly][tx + 1] = hy;
+            sH[2][ly][tx + 1] = hz;
+        }
+        // halo H on two warps: H_y, H_z at x0-1 (threads 0..BY-1), H_x, H_z at y0-1 (BY..BY+BX-1)
+        if (!r.bad) {
+            if (tid < BY) {
+                const int jh = y0 + tid, sy = tid + 1;
+                if (x0 > 0 && jh < p.ny) {
+                    const Cell h = make_cell(p, x0 - 1, jh, k, false);
+                    sH[1][sy][0] = h_cell<1, false, TF>(p, h, r.h(k, 1, sy, 3), r.e(k, 0, sy, 3),
+                                                        r.e(k + 1, 0, sy, 3), r.e(k, 2, sy, 3), r.e(k, 2, sy, 4),
+                                                        false);
+                    sH[2][sy][0] = h_cell<2, false, TF>(p, h, r.h(k, 2, sy, 3), r.e(k, 1, sy, 3), r.e(k, 1, sy, 4),
+                                                        r.e(k, 0, sy, 3), r.e(k, 0, sy + 1, 3), false);
+                }
+            } else if (tid < BY + BX) {
+                const int s0 = tid - BY, ih = x0 + s0, sx = s0 + 4;
+                if (y0 > 0 && ih < p.nx) {
+                    const Cell h = make_cell(p, ih, y0 - 1, k, false);
+                    sH[0][0][s0 + 1] = h_cell<0, false, TF>(p, h, r.h(k, 0, 0, sx), r.e(k, 2, 0, sx),
+                                                            r.e(k, 2, 1, sx), r.e(k, 1, 0, sx), r.e(k + 1, 1, 0, sx),
+                                                            false);
+                    sH[2][0][s0 + 1] = h_cell<2, false, TF>(p, h, r.h(k, 2, 0, sx), r.e(k, 1, 0, sx),
+                                                            r.e(k, 1, 0, sx + 1), r.e(k, 0, 0, sx), r.e(k, 0, 1, sx),
+                                                            false);
+                }
+            }
+        }
+        fail = __syncthreads_or(r.bad);
+        if (fail) break;
+        // E plane k and H plane k have had their last reader: refill their stages
+        if (tid == 0) {
+            if (k + 4 <= k1) r.issue_e(k + 4);
+            if (k + 3 < k1) r.issue_h(k + 3);
+        }
+        // f2 on the tile (reads only sH and registers); tangential E on the walls stays zero
+        if (in) {
+            const int ox = tx + 1;
+            const float hzm = sH[2][ly - 1][ox], hzi = sH[2][ly][ox - 1];
+            const float hyi = sH[1][ly][ox - 1], hxm = sH[0][ly - 1][ox];
+            if (TF) {
+                if (j >= 1 && k >= 1)
+                    e_cell<0, false, TF>(p, c, ex, hz, hzm, hy, hy_prev);
+                else
+                    p.E1[0][c.q] = 0.f;
+                if (i >= 1 && k >= 1)
+                    e_cell<1, false, TF>(p, c, ey, hx, hx_prev, hz, hzi);
+                else
+                    p.E1[1][c.q] = 0.f;
+                if (i >= 1 && j >= 1)
+                    e_cell<2, false, TF>(p, c, ez, hy, hyi, hx, hxm);
+                else
+                    p.E1[2][c.q] = 0.f;
+            } else {
+                p.E1[0][c.q] = (j >= 1 && k >= 1) ? ex + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
+                p.E1[1][c.q] = (i >= 1 && k >= 1) ? ey + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
+                p.E1[2][c.q] = (i >= 1 && j >= 1) ? ez + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
+            }
+        }
+        hx_prev = hx;
+        hy_prev = hy;
+        hb ^= 1;
+    }
+    if (fail && tid == 0) {
+        atomicOr(p.err, 4);
+        r.drain();
+    }
+}
+
 // Classes of the box [lo, hi] (cells, inclusive): does it touch a CPML slab,
 // or a cell on which a TF/SF conversion happens (within one cell of the TF
 // surface)?
@@ -729,8 +991,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, i
 // launched concurrently on two streams: k_step_pml takes the CPML tiles,
 // k_step the others (background and TF/SF), each block leaving at once if
 // its tile belongs to the other kernel.  Without CPML tiles k_step alone runs.
-// Separate kernels let the background tiles run with fewer registers and
-// without the psi staging area: 5 blocks per SM instead of 4.
+// Separate kernels let the background tiles run TMA-fed with fewer
+// registers and without the psi staging area: 5 blocks per SM instead of 4.
 template <bool PMLK, class SM>
 __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm)
 {
@@ -741,10 +1003,17 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
     bool pml, tf;
     tile_class(p, lo, hi, &pml, &tf);
     if (pml == PMLK) {
-        if (tf)
-            march<PMLK, true>(p, x0, y0, k0, k1, sm);
-        else
-            march<PMLK, false>(p, x0, y0, k0, k1, sm);
+        if constexpr (PMLK) {
+            if (tf)
+                march<true, true>(p, x0, y0, k0, k1, sm);
+            else
+                march<true, false>(p, x0, y0, k0, k1, sm);
+        } else {
+            if (tf)
+                march_tma<true>(p, x0, y0, k0, k1, sm);
+            else
+                march_tma<false>(p, x0, y0, k0, k1, sm);
+        }
     }
     // the 1D incident grid and the step counter: block (0,0,0) of k_step
     if (!PMLK && bx == 0 && by == 0 && bz == 0) {
@@ -756,7 +1025,7 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
 
 __global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
 {
-    __shared__ TileSharedBG sm;
+    __shared__ TileSharedTMA sm;
     step_tile_of<false>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
 }
 
