@@ -39,6 +39,7 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
                  int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
 void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
+void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st);
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st);
 void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
@@ -459,7 +460,7 @@ int encode_maps(nlf_ctx* c)
     const cuuint32_t elem[4] = {1, 1, 1, 1};
     for (int m = 0; m < 4; ++m) {
         const bool isE = m < 2;
-        const cuuint32_t box[4] = {NLF_TMA_BOX_X, isE ? NLF_TMA_BOX_EY : NLF_TMA_BOX_HY, 1, 3};
+        const cuuint32_t box[4] = {NLF_TMA_BOX_X, (cuuint32_t)(isE ? NLF_TMA_BOX_EY : NLF_TMA_BOX_HY), 1, 3};
         void* base = c->base + (isE ? c->off_E[m & 1] : c->off_H[m & 1]);
         CUresult r = encode(&c->tmaps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, elem,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -858,10 +859,16 @@ struct BatchPlan {
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     cudaStream_t cap = nullptr;
+    bool any_pml = false;             // some instance has CPML tiles: second kernel on aux
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     ~BatchPlan()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap) cudaStreamDestroy(cap);
+        if (aux) cudaStreamDestroy(aux);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
         if (dev) cudaFree(dev);
     }
 };
@@ -973,8 +980,19 @@ long long plan_launch(BatchPlan* P, cudaStream_t st)
     for (int s = 0; s < P->U; ++s) {
         nlf::BatchStep bs = P->bs;
         bs.launch_par = s & 1;
-        nlf::launch_step_batch(bs, P->items, st);
-        ++nodes;
+        if (P->any_pml) {
+            // CPML tiles on the plan's second stream, forked from and joined into st
+            cudaEventRecord(P->fork, st);
+            cudaStreamWaitEvent(P->aux, P->fork, 0);
+            nlf::launch_step_batch_pml(bs, P->items, P->aux);
+            nlf::launch_step_batch(bs, P->items, st);
+            cudaEventRecord(P->join, P->aux);
+            cudaStreamWaitEvent(st, P->join, 0);
+            nodes += 2;
+        } else {
+            nlf::launch_step_batch(bs, P->items, st);
+            ++nodes;
+        }
         if (P->met_sites > 0) {
             nlf::launch_metal_batch(bs, P->met_sites, st);
             ++nodes;
@@ -1037,6 +1055,16 @@ BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
     P->K = act[0]->K;
     P->B = act[0]->B;
     P->U = act[0]->U;
+    for (nlf_ctx* x : act)
+        if (nlf::step_has_pml(x->sp[0])) P->any_pml = true;
+    if (P->any_pml) {
+        if (cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming) != cudaSuccess) {
+            *rcode = fail(act[0], NLF_E_CUDA, "batch plan streams");
+            return nullptr;
+        }
+    }
     *rcode = plan_descriptors(P.get(), g_kz_best);
     if (*rcode) return nullptr;
     g_plans.push_back(std::move(P));

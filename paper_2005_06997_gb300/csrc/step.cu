@@ -9,13 +9,13 @@
 // halo) in shared memory, computes H^{n+1/2} of the tile plus the -x / -y
 // halo (the halo H is the only recomputed work), keeps H of plane k-1 in
 // registers, and then updates the background E of the tile.  Planes arrive
-// ahead of use: by TMA into a ring of shared-memory stages (background tiles)
-// or by register prefetch (CPML tiles, batched grids), the CPML psi operands
-// by cp.async.  E, H and psi_H are double buffered (generation n read, n+1
-// written), so tiles need no grid-wide barrier; every field crosses HBM once
-// per step apart from halos.  Tiles are classified once per block: clear of
-// the CPML slabs and of the TF/SF surface they run plain Yee arithmetic with
-// no per-cell tests.
+// ahead of use by TMA into a ring of shared-memory stages, the CPML psi
+// operands by cp.async.  E, H and psi_H are double buffered (generation n
+// read, n+1 written), so tiles need no grid-wide barrier; every field crosses
+// HBM once per step apart from halos.  Tiles are classified once per block:
+// clear of the CPML slabs and of the TF/SF surface they run plain Yee
+// arithmetic with no per-cell tests; CPML tiles run in their own kernel
+// (more shared memory: the psi staging area) concurrently with the others.
 //
 // The material update (k_metal): one thread per material E-site of a
 // compact list rewrites E^{n+1} there from the H^{n+1/2} just written and
@@ -38,6 +38,8 @@
 //
 // Offsets are 32-bit: the library rejects grids with 3 px ny nz >= 2^32.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "nlf_internal.h"
 
@@ -331,108 +333,6 @@ __device__ void inc_step(const StepParams& p, int tid, int nt)
 
 // ------------------------------------------------------------------ tiles
 
-// E^n of one plane held in registers between its load and its store to
-// shared memory: the thread's own cell and (threads 0..NHALO-1) one halo
-// cell: rows y0-1 and y0+BY, columns x0-1 and x0+BX, and the two corners the
-// halo H needs.
-struct PlaneRegs {
-    float in[3];
-    float halo[3];
-};
-
-constexpr int NHALO = 2 * BX + 2 * BY + 2;
-
-__device__ __forceinline__ void halo_cell(int tid, int x0, int y0, int* gi, int* gj, int* sx, int* sy)
-{
-    if (tid < BX) {                       // row y0 - 1
-        *gi = x0 + tid; *gj = y0 - 1; *sx = tid + 1; *sy = 0;
-    } else if (tid < 2 * BX) {            // row y0 + BY
-        *gi = x0 + tid - BX; *gj = y0 + BY; *sx = tid - BX + 1; *sy = BY + 1;
-    } else if (tid < 2 * BX + BY) {       // column x0 - 1
-        *gi = x0 - 1; *gj = y0 + tid - 2 * BX; *sx = 0; *sy = tid - 2 * BX + 1;
-    } else if (tid < 2 * BX + 2 * BY) {   // column x0 + BX
-        *gi = x0 + BX; *gj = y0 + tid - 2 * BX - BY; *sx = BX + 1; *sy = tid - 2 * BX - BY + 1;
-    } else if (tid == 2 * BX + 2 * BY) {  // corner (x0 - 1, y0 + BY)
-        *gi = x0 - 1; *gj = y0 + BY; *sx = 0; *sy = BY + 1;
-    } else {                              // corner (x0 + BX, y0 - 1)
-        *gi = x0 + BX; *gj = y0 - 1; *sx = BX + 1; *sy = 0;
-    }
-}
-
-__device__ __forceinline__ void plane_load(const StepParams& p, int x0, int y0, int kk, int tx, int ty, int tid,
-                                           PlaneRegs& r)
-{
-    const bool kin = kk >= 0 && kk < p.nz;
-    const uint32_t base = kin ? (uint32_t)kk * (uint32_t)p.ny * (uint32_t)p.px : 0u;
-    {
-        const int gi = x0 + tx, gj = y0 + ty;
-        const bool ok = kin && gi < p.nx && gj < p.ny;
-        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.px + (ok ? gi : 0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r.in[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
-    }
-    if (tid < NHALO) {
-        int gi, gj, sx, sy;
-        halo_cell(tid, x0, y0, &gi, &gj, &sx, &sy);
-        const bool ok = kin && gi >= 0 && gi < p.nx && gj >= 0 && gj < p.ny;
-        const uint32_t o = base + (uint32_t)(ok ? gj : 0) * p.px + (ok ? gi : 0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r.halo[c] = ok ? __ldg(p.E0[c] + o) : 0.f;
-    }
-}
-
-__device__ __forceinline__ void plane_store(float (*s)[BY + 2][BX + 2], const PlaneRegs& r, int x0, int y0, int tx,
-                                            int ty, int tid)
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) s[c][ty + 1][tx + 1] = r.in[c];
-    if (tid < NHALO) {
-        int gi, gj, sx, sy;
-        halo_cell(tid, x0, y0, &gi, &gj, &sx, &sy);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s[c][sy][sx] = r.halo[c];
-    }
-}
-
-// H^{n-1/2} of plane kk at the thread's own cell and, for the halo threads,
-// at its halo H cell (threads 0..BY-1: (x0-1, y0+tid) H_y, H_z;
-// BY..BY+BX-1: (x0+tid-BY, y0-1) H_x, H_z).
-struct HRegs {
-    float own[3];
-    float halo[2];
-};
-
-__device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int kk, int i, int j, bool in, int tid,
-                                       HRegs& r)
-{
-    const uint32_t plane = (uint32_t)p.px * (uint32_t)p.ny;
-    if (in) {
-        const uint32_t q = (uint32_t)kk * plane + (uint32_t)j * p.px + i;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r.own[c] = __ldg(p.H0[c] + q);
-    }
-    if (tid < BY) {
-        const int jh = y0 + tid;
-        if (x0 > 0 && jh < p.ny) {
-            const uint32_t q = (uint32_t)kk * plane + (uint32_t)jh * p.px + (x0 - 1);
-            r.halo[0] = __ldg(p.H0[1] + q);
-            r.halo[1] = __ldg(p.H0[2] + q);
-        }
-    } else if (tid < BY + BX) {
-        const int ih = x0 + tid - BY;
-        if (y0 > 0 && ih < p.nx) {
-            const uint32_t q = (uint32_t)kk * plane + (uint32_t)(y0 - 1) * p.px + ih;
-            r.halo[0] = __ldg(p.H0[0] + q);
-            r.halo[1] = __ldg(p.H0[2] + q);
-        }
-    }
-}
-
-// Three E planes (k, k+1 and the one being filled with k+2) and two H planes
-// (written at k, read by the E update of k) let each z step run with one
-// block barrier: the store of plane k+2 goes to the buffer of plane k-1, read
-// last before the previous barrier, and the H plane of k+1 goes to the buffer
-// read last by the E update of k-1.
 // CPML tiles stage the psi values of plane k+1 in shared memory with
 // asynchronous copies issued during plane k, so the slab's extra operands
 // arrive off the critical path.  Per thread (own cell), by component C:
@@ -441,12 +341,6 @@ __device__ __forceinline__ void h_load(const StepParams& p, int x0, int y0, int 
 struct PsiShared {
     float own[2][12][BX * BY];
     float halo[2][4][BX + BY];
-};
-
-struct TileShared {
-    float sE[3][3][BY + 2][BX + 2];
-    float sH[2][3][BY + 1][BX + 1];
-    PsiShared ps;
 };
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src)
@@ -518,165 +412,6 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
     cp_async_commit();
 }
 
-// Tile classes (uniform per block): PML = the tile or its halo reaches a
-// CPML slab; TF = it reaches the cells next to the TF/SF surface.  A tile of
-// neither class runs plain Yee arithmetic with no per-cell test.
-template <bool PML, bool TF, class SM>
-__device__ __forceinline__ void march(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
-{
-    float (*sE)[3][BY + 2][BX + 2] = sm.sE;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int i = x0 + tx, j = y0 + ty;
-    const bool in = i < p.nx && j < p.ny;
-    const int lx = tx + 1, ly = ty + 1;
-    // slab positions of the own column and of the halo cells (constant along z)
-    const int slx = PML ? slab_local(p, 0, i) : -1, sly = PML ? slab_local(p, 1, j) : -1;
-    float hx_prev = 0.f, hy_prev = 0.f;           // H_x, H_y of plane k-1, own column
-    PlaneRegs pr;
-    HRegs hr = {{0.f, 0.f, 0.f}, {0.f, 0.f}};
-    // buffers of planes k (cur), k+1 (nxt) and k-1 / k+2 (fre)
-    int cur = 0, nxt = 1, fre = 2;
-    plane_load(p, x0, y0, k0, tx, ty, tid, pr);
-    plane_store(sE[cur], pr, x0, y0, tx, ty, tid);
-    plane_load(p, x0, y0, k0 + 1, tx, ty, tid, pr);
-    plane_store(sE[nxt], pr, x0, y0, tx, ty, tid);
-    if (k0 > 0) {
-        plane_load(p, x0, y0, k0 - 1, tx, ty, tid, pr);
-        plane_store(sE[fre], pr, x0, y0, tx, ty, tid);
-        __syncthreads();
-        if (in) {
-            const Cell c = make_cell(p, i, j, k0 - 1, PML);
-            // psi_H of H_x (A1 = y, A2 = z) and H_y (A1 = z, A2 = x) at plane k0-1
-            float px1 = 0.f, px2 = 0.f, py1 = 0.f, py2 = 0.f;
-            if (PML) {
-                if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
-                if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
-                if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
-                if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
-            }
-            hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), sE[fre][2][ly][lx], sE[fre][2][ly + 1][lx],
-                                         sE[fre][1][ly][lx], sE[cur][1][ly][lx], false, px1, px2);
-            hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), sE[fre][0][ly][lx], sE[cur][0][ly][lx],
-                                         sE[fre][2][ly][lx], sE[fre][2][ly][lx + 1], false, py1, py2);
-        }
-    }
-    h_load(p, x0, y0, k0, i, j, in, tid, hr);
-    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
-    __syncthreads();
-    int hb = 0, pb = 0;
-    for (int k = k0; k < k1; ++k) {
-        float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
-        const bool more = k + 1 < k1;
-        // prefetch plane k+2 of E and plane k+1 of H^{n-1/2} (and of psi)
-        HRegs hn = hr;
-        if (more) {
-            plane_load(p, x0, y0, k + 2, tx, ty, tid, pr);
-            h_load(p, x0, y0, k + 1, i, j, in, tid, hn);
-        }
-        const float* po = nullptr;
-        const float* ph = nullptr;
-        if constexpr (PML) {
-            if (more) {
-                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, slx, sly, tid);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            po = &sm.ps.own[pb][0][tid];
-            ph = &sm.ps.halo[pb][0][tid < BY + BX ? tid : 0];
-        }
-        Cell c;
-        c.i = i;
-        c.j = j;
-        c.k = k;
-        c.q = ((uint32_t)k * p.ny + j) * p.px + i;
-        c.l[0] = slx;
-        c.l[1] = sly;
-        c.l[2] = PML ? slab_local(p, 2, k) : -1;
-        if (PML) cell_slabs(p, c);
-        float hx = 0.f, hy = 0.f, hz = 0.f;
-        float ex = 0.f, ey = 0.f, ez = 0.f;
-        // f1: own H^{n+1/2}
-        if (in) {
-            ex = sE[cur][0][ly][lx];
-            ey = sE[cur][1][ly][lx];
-            ez = sE[cur][2][ly][lx];
-            constexpr int S = BX * BY;
-            hx = h_cell<0, PML, TF>(p, c, hr.own[0], ez, sE[cur][2][ly + 1][lx], ey, sE[nxt][1][ly][lx], true,
-                                    PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f);
-            hy = h_cell<1, PML, TF>(p, c, hr.own[1], ex, sE[nxt][0][ly][lx], ez, sE[cur][2][ly][lx + 1], true,
-                                    PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f);
-            hz = h_cell<2, PML, TF>(p, c, hr.own[2], ey, sE[cur][1][ly][lx + 1], ex, sE[cur][0][ly + 1][lx], true,
-                                    PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f);
-            sH[0][ly][lx] = hx;
-            sH[1][ly][lx] = hy;
-            sH[2][ly][lx] = hz;
-        }
-        // halo H on two warps: H_y, H_z at x0-1 (threads 0..BY-1), H_x, H_z at y0-1 (BY..BY+BX-1)
-        if (tid < BY) {
-            const int jh = y0 + tid, sy = tid + 1;
-            if (x0 > 0 && jh < p.ny) {
-                const Cell h = make_cell(p, x0 - 1, jh, k, PML);
-                constexpr int S = BX + BY;
-                sH[1][sy][0] = h_cell<1, PML, TF>(p, h, hr.halo[0], sE[cur][0][sy][0], sE[nxt][0][sy][0],
-                                                  sE[cur][2][sy][0], sE[cur][2][sy][1], false,
-                                                  PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                sH[2][sy][0] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][sy][0], sE[cur][1][sy][1],
-                                                  sE[cur][0][sy][0], sE[cur][0][sy + 1][0], false,
-                                                  PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
-            }
-        } else if (tid < BY + BX) {
-            const int ih = x0 + tid - BY, sx = tid - BY + 1;
-            if (y0 > 0 && ih < p.nx) {
-                const Cell h = make_cell(p, ih, y0 - 1, k, PML);
-                constexpr int S = BX + BY;
-                sH[0][0][sx] = h_cell<0, PML, TF>(p, h, hr.halo[0], sE[cur][2][0][sx], sE[cur][2][1][sx],
-                                                  sE[cur][1][0][sx], sE[nxt][1][0][sx], false,
-                                                  PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                sH[2][0][sx] = h_cell<2, PML, TF>(p, h, hr.halo[1], sE[cur][1][0][sx], sE[cur][1][0][sx + 1],
-                                                  sE[cur][0][0][sx], sE[cur][0][1][sx], false,
-                                                  PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
-            }
-        }
-        if (more) plane_store(sE[fre], pr, x0, y0, tx, ty, tid);
-        __syncthreads();
-        // f2, f3, f4 on the tile (reads only sH and registers); tangential E on the walls stays zero
-        if (in) {
-            const float hzm = sH[2][ly - 1][lx], hzi = sH[2][ly][lx - 1];
-            const float hyi = sH[1][ly][lx - 1], hxm = sH[0][ly - 1][lx];
-            if (PML || TF) {
-                constexpr int S = BX * BY;
-                if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
-                else
-                    p.E1[0][c.q] = 0.f;
-                if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
-                else
-                    p.E1[1][c.q] = 0.f;
-                if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
-                else
-                    p.E1[2][c.q] = 0.f;
-            } else {
-                // background: eps_b dE = S curl H
-                p.E1[0][c.q] = (j >= 1 && k >= 1) ? ex + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
-                p.E1[1][c.q] = (i >= 1 && k >= 1) ? ey + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
-                p.E1[2][c.q] = (i >= 1 && j >= 1) ? ez + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
-            }
-        }
-        hx_prev = hx;
-        hy_prev = hy;
-        hr = hn;
-        const int t = cur;
-        cur = nxt;
-        nxt = fre;
-        fre = t;
-        hb ^= 1;
-        pb ^= 1;
-    }
-}
-
 // ------------------------------------------------------- TMA-fed z march
 //
 // The background tiles (no CPML) take their E^n and H^{n-1/2} planes from
@@ -696,15 +431,21 @@ constexpr int TMA_E_FLOATS = 3 * TMA_EY * TMA_EX;
 constexpr int TMA_H_FLOATS = 3 * TMA_HY * TMA_EX;
 constexpr int TMA_E_STAGE = (TMA_E_FLOATS * 4 + 127) / 128 * 32;   // floats, 128-byte multiple
 constexpr int TMA_H_STAGE = (TMA_H_FLOATS * 4 + 127) / 128 * 32;
-constexpr int NE_STAGE = 4, NH_STAGE = 3;
+constexpr int NE_STAGE = 4, NH_STAGE = 3;      // background tiles
+constexpr int NE_PML = 3, NH_PML = 2, PML_BLOCKS = 4;   // CPML tiles (also stage psi): 4 blocks per SM
 constexpr long long TMA_SPIN = 1LL << 21;      // bounded mbarrier wait (~2 s at the hint below)
 
+struct NoPsi {};
+
+template <int NE, int NH, bool PML>
 struct TileSharedTMA {
-    alignas(128) float sE[NE_STAGE][TMA_E_STAGE];
-    alignas(128) float sHo[NH_STAGE][TMA_H_STAGE];
+    static constexpr int kNE = NE, kNH = NH;
+    alignas(128) float sE[NE][TMA_E_STAGE];
+    alignas(128) float sHo[NH][TMA_H_STAGE];
     float sH[2][3][BY + 1][BX + 1];
-    unsigned long long barE[NE_STAGE];
-    unsigned long long barH[NH_STAGE];
+    unsigned long long barE[NE];
+    unsigned long long barH[NH];
+    typename std::conditional<PML, PsiShared, NoPsi>::type ps;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
@@ -755,16 +496,20 @@ __device__ __forceinline__ void tma_plane(float* dst, const void* map, int x, in
 // by plane index.  Thread 0 also records which stages hold a copy not yet
 // waited for, so that after a timed-out wait it can let the copies in flight
 // land before the block exits.
+template <class SM>
 struct TmaRing {
-    TileSharedTMA& sm;
+    static constexpr int NE = SM::kNE, NH = SM::kNH;
+    SM& sm;
     const StepParams& p;
     int k0, x0, y0;
     unsigned pendE = 0, parE = 0, pendH = 0, parH = 0;
     bool bad = false;
-    __device__ int eslot(int pl) const { return (pl - k0 + 1) & 3; }
-    __device__ unsigned epar(int pl) const { return (unsigned)(((pl - k0 + 1) >> 2) & 1); }
-    __device__ int hslot(int pl) const { return (pl - k0) % 3; }
-    __device__ unsigned hpar(int pl) const { return (unsigned)(((pl - k0) / 3) & 1); }
+    // E plane pl lives in stage (pl - k0 + 1) mod NE, H plane pl in (pl - k0) mod NH;
+    // the parity is that of the stage's use count
+    __device__ int eslot(int pl) const { return (pl - k0 + 1) % NE; }
+    __device__ unsigned epar(int pl) const { return (unsigned)(((pl - k0 + 1) / NE) & 1); }
+    __device__ int hslot(int pl) const { return (pl - k0) % NH; }
+    __device__ unsigned hpar(int pl) const { return (unsigned)(((pl - k0) / NH) & 1); }
     __device__ void issue_e(int pl)
     {
         const int q = eslot(pl);
@@ -800,99 +545,135 @@ struct TmaRing {
     // thread 0, after a block-wide failure: wait (bounded) for what is in flight
     __device__ void drain()
     {
-        for (int q = 0; q < NE_STAGE; ++q)
+        for (int q = 0; q < NE; ++q)
             if (pendE >> q & 1u) mbar_wait(&sm.barE[q], parE >> q & 1u);
-        for (int q = 0; q < NH_STAGE; ++q)
+        for (int q = 0; q < NH; ++q)
             if (pendH >> q & 1u) mbar_wait(&sm.barH[q], parH >> q & 1u);
     }
 };
 
-template <bool TF>
-__device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, TileSharedTMA& sm)
+// The z march of one tile over planes [k0, k1).  Template classes, uniform
+// per block: PML = the tile or its halo reaches a CPML slab (psi arithmetic,
+// psi staged by cp.async); TF = it reaches the cells next to the TF/SF
+// surface (incident-field corrections).
+template <bool PML, bool TF, class SM>
+__device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
 {
+    constexpr int NE = SM::kNE, NH = SM::kNH;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
     const int lx = tx + 4, ly = ty + 1;               // own cell in an E or H stage
-    TmaRing r{sm, p, k0, x0, y0};
+    // slab positions of the own column (constant along z)
+    const int slx = PML ? slab_local(p, 0, i) : -1, sly = PML ? slab_local(p, 1, j) : -1;
+    TmaRing<SM> r{sm, p, k0, x0, y0};
     if (tid == 0) {
-        for (int q = 0; q < NE_STAGE; ++q) mbar_init(&sm.barE[q]);
-        for (int q = 0; q < NH_STAGE; ++q) mbar_init(&sm.barH[q]);
+        for (int q = 0; q < NE; ++q) mbar_init(&sm.barE[q]);
+        for (int q = 0; q < NH; ++q) mbar_init(&sm.barH[q]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         // the tensor maps were written to device memory by a copy, not by this proxy
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmE) : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmH) : "memory");
     }
     __syncthreads();
-    // E planes k0-1 .. k0+2 and H planes k0 .. k0+2 (E is needed up to plane k1, H up to k1-1)
+    // E planes k0-1 .. k0+NE-2 and H planes k0 .. k0+NH-1 (E is needed up to plane k1, H up to k1-1)
     if (tid == 0) {
-        for (int pl = k0 - 1; pl <= k0 + 2 && pl <= k1; ++pl) r.issue_e(pl);
-        for (int pl = k0; pl <= k0 + 2 && pl < k1; ++pl) r.issue_h(pl);
+        for (int pl = k0 - 1; pl <= k0 + NE - 2 && pl <= k1; ++pl) r.issue_e(pl);
+        for (int pl = k0; pl <= k0 + NH - 1 && pl < k1; ++pl) r.issue_h(pl);
     }
     // H_x, H_y of plane k0-1 (own column) for the first E update
     float hx_prev = 0.f, hy_prev = 0.f;
     r.wait_e(k0 - 1);
     r.wait_e(k0);
     if (!r.bad && k0 > 0 && in) {
-        const Cell c = make_cell(p, i, j, k0 - 1, false);
+        const Cell c = make_cell(p, i, j, k0 - 1, PML);
         const int pm = k0 - 1;
-        hx_prev = h_cell<0, false, TF>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
-                                       r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false);
-        hy_prev = h_cell<1, false, TF>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
-                                       r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false);
+        // psi_H of H_x (A1 = y, A2 = z) and H_y (A1 = z, A2 = x) at plane k0-1
+        float px1 = 0.f, px2 = 0.f, py1 = 0.f, py2 = 0.f;
+        if (PML) {
+            if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
+            if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
+            if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
+            if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
+        }
+        hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
+                                     r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2);
+        hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
+                                     r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2);
     }
+    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
     bool fail = __syncthreads_or(r.bad);
-    if (!fail && tid == 0 && k0 + 3 <= k1) r.issue_e(k0 + 3);
-    int hb = 0;
+    if (!fail && tid == 0 && k0 + NE - 1 <= k1) r.issue_e(k0 + NE - 1);
+    int hb = 0, pb = 0;
     for (int k = k0; k < k1 && !fail; ++k) {
         float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
+        const bool more = k + 1 < k1;
         r.wait_e(k + 1);
         r.wait_h(k);
+        const float* po = nullptr;
+        const float* ph = nullptr;
+        if constexpr (PML) {
+            // psi of plane k+1 on its way while plane k is computed
+            if (more) {
+                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, slx, sly, tid);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            po = &sm.ps.own[pb][0][tid];
+            ph = &sm.ps.halo[pb][0][tid < BY + BX ? tid : 0];
+        }
         Cell c;
         c.i = i;
         c.j = j;
         c.k = k;
         c.q = ((uint32_t)k * p.ny + j) * p.px + i;
-        c.l[0] = c.l[1] = c.l[2] = -1;
+        c.l[0] = slx;
+        c.l[1] = sly;
+        c.l[2] = PML ? slab_local(p, 2, k) : -1;
+        if (PML) cell_slabs(p, c);
         float hx = 0.f, hy = 0.f, hz = 0.f;
         float ex = 0.f, ey = 0.f, ez = 0.f;
         // f1: own H^{n+1/2}
         if (in && !r.bad) {
+            constexpr int S = BX * BY;
             ex = r.e(k, 0, ly, lx);
             ey = r.e(k, 1, ly, lx);
             ez = r.e(k, 2, ly, lx);
-            hx = h_cell<0, false, TF>(p, c, r.h(k, 0, ly, lx), ez, r.e(k, 2, ly + 1, lx), ey, r.e(k + 1, 1, ly, lx),
-                                      true);
-            hy = h_cell<1, false, TF>(p, c, r.h(k, 1, ly, lx), ex, r.e(k + 1, 0, ly, lx), ez, r.e(k, 2, ly, lx + 1),
-                                      true);
-            hz = h_cell<2, false, TF>(p, c, r.h(k, 2, ly, lx), ey, r.e(k, 1, ly, lx + 1), ex, r.e(k, 0, ly + 1, lx),
-                                      true);
+            hx = h_cell<0, PML, TF>(p, c, r.h(k, 0, ly, lx), ez, r.e(k, 2, ly + 1, lx), ey, r.e(k + 1, 1, ly, lx),
+                                    true, PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f);
+            hy = h_cell<1, PML, TF>(p, c, r.h(k, 1, ly, lx), ex, r.e(k + 1, 0, ly, lx), ez, r.e(k, 2, ly, lx + 1),
+                                    true, PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f);
+            hz = h_cell<2, PML, TF>(p, c, r.h(k, 2, ly, lx), ey, r.e(k, 1, ly, lx + 1), ex, r.e(k, 0, ly + 1, lx),
+                                    true, PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f);
             sH[0][ly][tx + 1] = hx;
             sH[1][ly][tx + 1] = hy;
             sH[2][ly][tx + 1] = hz;
         }
         // halo H on two warps: H_y, H_z at x0-1 (threads 0..BY-1), H_x, H_z at y0-1 (BY..BY+BX-1)
         if (!r.bad) {
+            constexpr int S = BX + BY;
             if (tid < BY) {
                 const int jh = y0 + tid, sy = tid + 1;
                 if (x0 > 0 && jh < p.ny) {
-                    const Cell h = make_cell(p, x0 - 1, jh, k, false);
-                    sH[1][sy][0] = h_cell<1, false, TF>(p, h, r.h(k, 1, sy, 3), r.e(k, 0, sy, 3),
-                                                        r.e(k + 1, 0, sy, 3), r.e(k, 2, sy, 3), r.e(k, 2, sy, 4),
-                                                        false);
-                    sH[2][sy][0] = h_cell<2, false, TF>(p, h, r.h(k, 2, sy, 3), r.e(k, 1, sy, 3), r.e(k, 1, sy, 4),
-                                                        r.e(k, 0, sy, 3), r.e(k, 0, sy + 1, 3), false);
+                    const Cell h = make_cell(p, x0 - 1, jh, k, PML);
+                    sH[1][sy][0] = h_cell<1, PML, TF>(p, h, r.h(k, 1, sy, 3), r.e(k, 0, sy, 3), r.e(k + 1, 0, sy, 3),
+                                                      r.e(k, 2, sy, 3), r.e(k, 2, sy, 4), false,
+                                                      PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
+                    sH[2][sy][0] = h_cell<2, PML, TF>(p, h, r.h(k, 2, sy, 3), r.e(k, 1, sy, 3), r.e(k, 1, sy, 4),
+                                                      r.e(k, 0, sy, 3), r.e(k, 0, sy + 1, 3), false,
+                                                      PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
                 }
             } else if (tid < BY + BX) {
                 const int s0 = tid - BY, ih = x0 + s0, sx = s0 + 4;
                 if (y0 > 0 && ih < p.nx) {
-                    const Cell h = make_cell(p, ih, y0 - 1, k, false);
-                    sH[0][0][s0 + 1] = h_cell<0, false, TF>(p, h, r.h(k, 0, 0, sx), r.e(k, 2, 0, sx),
-                                                            r.e(k, 2, 1, sx), r.e(k, 1, 0, sx), r.e(k + 1, 1, 0, sx),
-                                                            false);
-                    sH[2][0][s0 + 1] = h_cell<2, false, TF>(p, h, r.h(k, 2, 0, sx), r.e(k, 1, 0, sx),
-                                                            r.e(k, 1, 0, sx + 1), r.e(k, 0, 0, sx), r.e(k, 0, 1, sx),
-                                                            false);
+                    const Cell h = make_cell(p, ih, y0 - 1, k, PML);
+                    sH[0][0][s0 + 1] = h_cell<0, PML, TF>(p, h, r.h(k, 0, 0, sx), r.e(k, 2, 0, sx), r.e(k, 2, 1, sx),
+                                                          r.e(k, 1, 0, sx), r.e(k + 1, 1, 0, sx), false,
+                                                          PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
+                    sH[2][0][s0 + 1] = h_cell<2, PML, TF>(p, h, r.h(k, 2, 0, sx), r.e(k, 1, 0, sx),
+                                                          r.e(k, 1, 0, sx + 1), r.e(k, 0, 0, sx), r.e(k, 0, 1, sx),
+                                                          false, PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
                 }
             }
         }
@@ -900,25 +681,26 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         if (fail) break;
         // E plane k and H plane k have had their last reader: refill their stages
         if (tid == 0) {
-            if (k + 4 <= k1) r.issue_e(k + 4);
-            if (k + 3 < k1) r.issue_h(k + 3);
+            if (k + NE <= k1) r.issue_e(k + NE);
+            if (k + NH < k1) r.issue_h(k + NH);
         }
         // f2 on the tile (reads only sH and registers); tangential E on the walls stays zero
         if (in) {
             const int ox = tx + 1;
             const float hzm = sH[2][ly - 1][ox], hzi = sH[2][ly][ox - 1];
             const float hyi = sH[1][ly][ox - 1], hxm = sH[0][ly - 1][ox];
-            if (TF) {
+            if (PML || TF) {
+                constexpr int S = BX * BY;
                 if (j >= 1 && k >= 1)
-                    e_cell<0, false, TF>(p, c, ex, hz, hzm, hy, hy_prev);
+                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, false, TF>(p, c, ey, hx, hx_prev, hz, hzi);
+                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, false, TF>(p, c, ez, hy, hyi, hx, hxm);
+                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -930,11 +712,13 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         hx_prev = hx;
         hy_prev = hy;
         hb ^= 1;
+        pb ^= 1;
     }
     if (fail && tid == 0) {
         atomicOr(p.err, 4);
         r.drain();
     }
+    if constexpr (PML) cp_async_wait<0>();
 }
 
 // Classes of the box [lo, hi] (cells, inclusive): does it touch a CPML slab,
@@ -957,35 +741,6 @@ __device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3],
     *tf = p.tfsf && !inner && !outer;
 }
 
-// One tile (bx, by) and z chunk bz of the fused step; every thread of the
-// block must call it (it synchronises the block).  The tile (0,0,0) also
-// advances the 1D incident grid and the step counter.
-__device__ __forceinline__ void step_tile(const StepParams& p, int bx, int by, int bz, int kz, TileShared& sm)
-{
-    const int x0 = bx * BX, y0 = by * BY;
-    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
-    const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
-    const int hi[3] = {x0 + BX, y0 + BY, k1};
-    bool pml, tf;
-    tile_class(p, lo, hi, &pml, &tf);
-    if (pml) {
-        if (tf)
-            march<true, true>(p, x0, y0, k0, k1, sm);
-        else
-            march<true, false>(p, x0, y0, k0, k1, sm);
-    } else {
-        if (tf)
-            march<false, true>(p, x0, y0, k0, k1, sm);
-        else
-            march<false, false>(p, x0, y0, k0, k1, sm);
-    }
-    if (bx == 0 && by == 0 && bz == 0) {
-        const int tid = threadIdx.y * BX + threadIdx.x;
-        if (p.tfsf) inc_step(p, tid, BX * BY);
-        if (tid == 0) *p.step1 = *p.step0 + 1;
-    }
-    __syncthreads();
-}
 
 // The single-grid step runs as two kernels over the same grid of tiles,
 // launched concurrently on two streams: k_step_pml takes the CPML tiles,
@@ -1003,17 +758,10 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
     bool pml, tf;
     tile_class(p, lo, hi, &pml, &tf);
     if (pml == PMLK) {
-        if constexpr (PMLK) {
-            if (tf)
-                march<true, true>(p, x0, y0, k0, k1, sm);
-            else
-                march<true, false>(p, x0, y0, k0, k1, sm);
-        } else {
-            if (tf)
-                march_tma<true>(p, x0, y0, k0, k1, sm);
-            else
-                march_tma<false>(p, x0, y0, k0, k1, sm);
-        }
+        if (tf)
+            march_tma<PMLK, true>(p, x0, y0, k0, k1, sm);
+        else
+            march_tma<PMLK, false>(p, x0, y0, k0, k1, sm);
     }
     // the 1D incident grid and the step counter: block (0,0,0) of k_step
     if (!PMLK && bx == 0 && by == 0 && bz == 0) {
@@ -1023,15 +771,22 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
     }
 }
 
+using SharedBG = TileSharedTMA<NE_STAGE, NH_STAGE, false>;
+using SharedPML = TileSharedTMA<NE_PML, NH_PML, true>;
+
 __global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
 {
-    __shared__ TileSharedTMA sm;
+    __shared__ SharedBG sm;
     step_tile_of<false>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
 }
 
-__global__ void __launch_bounds__(BX * BY, 4) k_step_pml(const StepParams p, int kz)
+// CPML tiles: TMA rings plus the psi staging area exceed the 48 KB of static
+// shared memory, so the block's area is dynamic (aligned here to 128 bytes).
+__global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_pml(const StepParams p, int kz)
 {
-    __shared__ TileShared sm;
+    extern __shared__ unsigned char nlf_dyn_smem[];
+    const unsigned mis = smem_u32(nlf_dyn_smem) & 127u;
+    SharedPML& sm = *reinterpret_cast<SharedPML*>(nlf_dyn_smem + ((128u - mis) & 127u));
     step_tile_of<true>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
 }
 
@@ -1051,57 +806,78 @@ __device__ __forceinline__ int find_inst(const long long* end, int n, long long 
     return lo;
 }
 
-// A persistent grid walks the work items (instance, tile, z chunk) of every
-// instance; each item runs the single-grid tile code with that instance's
-// parameters staged in shared memory.
-__global__ void __launch_bounds__(BX * BY, 4) k_step_batch(const BatchStep a)
+// Batched grids: one block per work item (instance, tile, z chunk) of the
+// concatenated list of every instance.  As for a single grid, two kernels
+// take the list concurrently, k_step_batch the background and TF/SF tiles
+// (TMA-fed) and k_step_batch_pml the CPML tiles, each block leaving at once if
+// its tile belongs to the other kernel.  A block stages its instance's
+// parameters in shared memory first.
+template <bool PMLK, class SM>
+__device__ __forceinline__ void batch_item(const BatchStep& a, SM& sm, StepParams& sp)
 {
-    __shared__ TileShared sm;
-    __shared__ StepParams sp;
-    __shared__ long long s_end[NLF_MAX_BATCH];
     const int tid = threadIdx.y * BX + threadIdx.x;
-    for (int q = tid; q < a.n; q += BX * BY) s_end[q] = a.item_end[q];
+    const long long w = blockIdx.x;
+    const int q = find_inst(a.item_end, a.n, w);
+    const BatchInst& I = a.inst[q];
+    const int par = I.base_par ^ a.launch_par;
+    const int* src = reinterpret_cast<const int*>(&a.params[2 * q + par]);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int t = tid; t < (int)(sizeof(StepParams) / sizeof(int)); t += BX * BY) dst[t] = src[t];
     __syncthreads();
-    const long long total = s_end[a.n - 1];
-    int loaded = -1;
-    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
-        const int q = find_inst(s_end, a.n, w);
-        const BatchInst& I = a.inst[q];
-        if (q != loaded) {
-            const int par = I.base_par ^ a.launch_par;
-            const int* src = reinterpret_cast<const int*>(&a.params[2 * q + par]);
-            int* dst = reinterpret_cast<int*>(&sp);
-            for (int t = tid; t < (int)(sizeof(StepParams) / sizeof(int)); t += BX * BY) dst[t] = src[t];
-            __syncthreads();
-            loaded = q;
-        }
-        const long long r = w - (q > 0 ? s_end[q - 1] : 0);
-        const long long per_plane = (long long)I.tiles_x * I.tiles_y;
-        const int bz = (int)(r / per_plane);
-        const long long rem = r - bz * per_plane;
-        const int by = (int)(rem / I.tiles_x);
-        const int bx = (int)(rem - (long long)by * I.tiles_x);
-        step_tile(sp, bx, by, bz, I.kz, sm);
-    }
+    const long long r = w - (q > 0 ? a.item_end[q - 1] : 0);
+    const long long per_plane = (long long)I.tiles_x * I.tiles_y;
+    const int bz = (int)(r / per_plane);
+    const long long rem = r - bz * per_plane;
+    const int by = (int)(rem / I.tiles_x);
+    const int bx = (int)(rem - (long long)by * I.tiles_x);
+    step_tile_of<PMLK>(sp, bx, by, bz, I.kz, sm);
 }
 
-int batch_blocks()
+__global__ void __launch_bounds__(BX * BY, 5) k_step_batch(const BatchStep a)
 {
-    static int nb = 0;
-    if (nb == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_batch, BX * BY, 0);
-        nb = sms * (per > 0 ? per : 1);
+    __shared__ SharedBG sm;
+    __shared__ StepParams sp;
+    batch_item<false>(a, sm, sp);
+}
+
+constexpr size_t kPmlSpOff = (sizeof(SharedPML) + 127) / 128 * 128;
+
+__global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_batch_pml(const BatchStep a)
+{
+    extern __shared__ unsigned char nlf_dyn_smem[];
+    const unsigned mis = smem_u32(nlf_dyn_smem) & 127u;
+    unsigned char* base = nlf_dyn_smem + ((128u - mis) & 127u);
+    SharedPML& sm = *reinterpret_cast<SharedPML*>(base);
+    StepParams& sp = *reinterpret_cast<StepParams*>(base + kPmlSpOff);
+    batch_item<true>(a, sm, sp);
+}
+
+// Dynamic shared memory above 48 KB must be granted per kernel and device.
+template <class K>
+void grant_smem(K kernel, size_t bytes, bool* granted)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !granted[dev]) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+            dev >= 0 && dev < 64)
+            granted[dev] = true;
     }
-    return nb;
 }
 
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st)
 {
-    const long long g = total_items < batch_blocks() ? total_items : batch_blocks();
-    k_step_batch<<<(unsigned)g, dim3(BX, BY, 1), 0, st>>>(a);
+    if (total_items <= 0) return;
+    k_step_batch<<<(unsigned)total_items, dim3(BX, BY, 1), 0, st>>>(a);
+}
+
+void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st)
+{
+    if (total_items <= 0) return;
+    constexpr size_t smem = kPmlSpOff + sizeof(StepParams) + 128;
+    static bool granted[64] = {};
+    grant_smem(k_step_batch_pml, smem, granted);
+    k_step_batch_pml<<<(unsigned)total_items, dim3(BX, BY, 1), smem, st>>>(a);
 }
 
 // Batched material update: grid-stride over the material site lists of every
@@ -1155,9 +931,12 @@ void launch_step(const StepParams& p, cudaStream_t st)
 void launch_step_pml(const StepParams& p, cudaStream_t st)
 {
     const int kz = step_kz(p);
+    constexpr size_t smem = sizeof(SharedPML) + 128;
+    static bool granted[64] = {};
+    grant_smem(k_step_pml, smem, granted);
     dim3 blk(BX, BY, 1);
     dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
-    k_step_pml<<<grd, blk, 0, st>>>(p, kz);
+    k_step_pml<<<grd, blk, smem, st>>>(p, kz);
 }
 
 }  // namespace nlf
