@@ -16,9 +16,9 @@ explicit L2 flush is needed between steps.
            device->host read of the spectra, timed on the host
   roofline - the EM step kernel k_step (the dominant kernel): algorithmic
            bytes per launch over its mean CUDA-event duration (events around
-           each kernel of the last 64 time steps of each solve, launched one
-           at a time) against the measured HBM copy bandwidth; the material
-           update and DFT kernels are reported beside it
+           each kernel of the last 64 time steps of each solve, replayed as
+           one CUDA graph) against the measured HBM copy bandwidth; the
+           material update and DFT kernels are reported beside it
   cpu_baseline - the FP64 CPU oracle on a bounded sample of the same workload
   serving - solves/s and p50/p99 latency of the seeded request stream's first
            requests, continuous batching against one grid at a time
@@ -177,7 +177,7 @@ def run_ours(args, rank, world, dist):
         solver.reset(sp)
         solver.run(steps - tail, sp)
         if record_kernel_times is not None:
-            # the last steps one launch at a time, CUDA events around each kernel
+            # the last steps with CUDA events around each kernel (one captured graph)
             record_kernel_times.append(solver.time_kernels(tail, sp))
         else:
             solver.run(tail, sp)

@@ -1312,21 +1312,40 @@ int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
             release();
             return fail(c, NLF_E_CUDA, "event creation failed");
         }
+    // the instrumented steps are captured and replayed once as a graph, the
+    // way nlf_run executes steps, so that launch overheads of eager launches
+    // (and of the fork / join of the CPML kernel) do not enter the figures
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        release();
+        return fail(c, NLF_E_CUDA, "capture stream");
+    }
+    cudaError_t err = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) {
+        release();
+        return fail(c, NLF_E_CUDA, "kernel timing capture: %s", cudaGetErrorString(err));
+    }
     for (long long s = 0; s < steps; ++s) {
         cudaEvent_t* e = &ev[(size_t)(4 * s)];
-        cudaEventRecord(e[0], st);
-        launch_em(c, st);
-        cudaEventRecord(e[1], st);
+        cudaEventRecord(e[0], c->cap);
+        launch_em(c, c->cap);
+        cudaEventRecord(e[1], c->cap);
         if (c->n_msites > 0) {
-            nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
+            nlf::launch_metal(c->sp[c->n & 1], c->n_msites, c->cap);
             c->launches += 1;
         }
-        cudaEventRecord(e[2], st);
+        cudaEventRecord(e[2], c->cap);
         c->n += 1;
-        monitor_work(c, st);
-        cudaEventRecord(e[3], st);
+        monitor_work(c, c->cap);
+        cudaEventRecord(e[3], c->cap);
     }
-    cudaError_t err = cudaEventSynchronize(ev.back());
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    err = cudaStreamEndCapture(c->cap, &g);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&x, g, 0);
+    if (err == cudaSuccess) err = cudaGraphLaunch(x, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
     double acc[3] = {0.0, 0.0, 0.0};
     for (long long s = 0; s < steps && err == cudaSuccess; ++s) {
         cudaEvent_t* e = &ev[(size_t)(4 * s)];

@@ -267,8 +267,8 @@ class Solver:
         _check(self.h, self.L.nlf_run(self.h, int(steps), s))
 
     def time_kernels(self, steps: int, stream=None) -> dict:
-        """Advance `steps` steps one launch at a time with CUDA events around
-        each kernel; summed device ms per kernel class."""
+        """Advance `steps` steps (replayed as one CUDA graph) with CUDA events
+        around each kernel; summed device ms per kernel class."""
         s = C.c_void_p(int(stream) if stream is not None else 0)
         ms = (C.c_double * 3)()
         _check(self.h, self.L.nlf_time_kernels(self.h, int(steps), s, ms))
