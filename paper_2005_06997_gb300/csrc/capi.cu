@@ -1314,7 +1314,8 @@ int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
         }
     // the instrumented steps are captured and replayed once as a graph, the
     // way nlf_run executes steps, so that launch overheads of eager launches
-    // (and of the fork / join of the CPML kernel) do not enter the figures
+    // (and of the fork / join of the CPML kernel) do not enter the figures; the timing events are recorded as external event nodes (a plain record
+    // inside a capture only orders streams)
     if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
         release();
         return fail(c, NLF_E_CUDA, "capture stream");
@@ -1326,17 +1327,17 @@ int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
     }
     for (long long s = 0; s < steps; ++s) {
         cudaEvent_t* e = &ev[(size_t)(4 * s)];
-        cudaEventRecord(e[0], c->cap);
+        cudaEventRecordWithFlags(e[0], c->cap, cudaEventRecordExternal);
         launch_em(c, c->cap);
-        cudaEventRecord(e[1], c->cap);
+        cudaEventRecordWithFlags(e[1], c->cap, cudaEventRecordExternal);
         if (c->n_msites > 0) {
             nlf::launch_metal(c->sp[c->n & 1], c->n_msites, c->cap);
             c->launches += 1;
         }
-        cudaEventRecord(e[2], c->cap);
+        cudaEventRecordWithFlags(e[2], c->cap, cudaEventRecordExternal);
         c->n += 1;
         monitor_work(c, c->cap);
-        cudaEventRecord(e[3], c->cap);
+        cudaEventRecordWithFlags(e[3], c->cap, cudaEventRecordExternal);
     }
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
