@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include "nlf_internal.h"
+#include "dft_accum.cuh"
 
 namespace nlf {
 
@@ -136,11 +137,10 @@ __global__ void k_dft_phase(const DftParams d, int count)
     d.phase[t] = v;
 }
 
-// acc[r][f] += sum_s sample[s][r] * exp(i phase[s][f]) for the B buffered
-// samples: FP32 products within one block of samples, FP64 accumulation.
-// Block: blockDim.x frequencies of one frequency chunk x RCH records.
+// One flush of the running DFT: block = up to 256 frequencies of one
+// frequency chunk x RCH records (accum_records).
 template <int B, int RCH>
-__global__ void __launch_bounds__(128) k_dft_accum(const DftParams d)
+__global__ void __launch_bounds__(256) k_dft_accum(const DftParams d)
 {
     __shared__ float sE[B][RCH];
     __shared__ float sH[B][RCH];
@@ -155,35 +155,7 @@ __global__ void __launch_bounds__(128) k_dft_accum(const DftParams d)
     }
     __syncthreads();
     if (f >= d.nf) return;
-    float ce[B], se[B], ch[B], sh[B];
-#pragma unroll
-    for (int s = 0; s < B; ++s) {
-        const float4 v = d.phase[s * d.nf + f];
-        ce[s] = v.x;
-        se[s] = v.y;
-        ch[s] = v.z;
-        sh[s] = v.w;
-    }
-    const int rmax = (int)min((long long)RCH, nr - r0);
-    for (int rr = 0; rr < rmax; ++rr) {
-        float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
-#pragma unroll
-        for (int s = 0; s < B; ++s) {
-            const float e = sE[s][rr], h = sH[s][rr];
-            er = fmaf(e, ce[s], er);
-            ei = fmaf(e, se[s], ei);
-            hr = fmaf(h, ch[s], hr);
-            hi = fmaf(h, sh[s], hi);
-        }
-        const long long a = (r0 + rr) * d.nf + f;
-        double2 ae = d.accE[a], ah = d.accH[a];
-        ae.x += (double)er;
-        ae.y += (double)ei;
-        ah.x += (double)hr;
-        ah.y += (double)hi;
-        d.accE[a] = ae;
-        d.accH[a] = ah;
-    }
+    accum_records<B, RCH>(d, r0, f, sE, sH);
 }
 
 void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
@@ -195,16 +167,19 @@ void launch_dft_gather(const DftParams& d, const float* E, const float* H, const
 
 void launch_dft_flush(const DftParams& d, int count, cudaStream_t st)
 {
-    const int nt = d.B * d.nf;
-    k_dft_phase<<<(nt + 255) / 256, 256, 0, st>>>(d, count);
+    const int np = d.B * d.nf;
+    k_dft_phase<<<(np + 255) / 256, 256, 0, st>>>(d, count);
     constexpr int RCH = 32;
-    dim3 grd((unsigned)((d.nrec + 1 + RCH - 1) / RCH), (d.nf + 127) / 128);
+    // one frequency chunk of up to 256 threads (whole warps) per block row
+    const int chunks = (d.nf + 255) / 256;
+    const int nt = ((d.nf + chunks - 1) / chunks + 31) / 32 * 32;
+    dim3 grd((unsigned)((d.nrec + 1 + RCH - 1) / RCH), (unsigned)((d.nf + nt - 1) / nt));
     if (d.B <= 8)
-        k_dft_accum<8, RCH><<<grd, 128, 0, st>>>(d);
+        k_dft_accum<8, RCH><<<grd, nt, 0, st>>>(d);
     else if (d.B <= 16)
-        k_dft_accum<16, RCH><<<grd, 128, 0, st>>>(d);
+        k_dft_accum<16, RCH><<<grd, nt, 0, st>>>(d);
     else
-        k_dft_accum<32, RCH><<<grd, 128, 0, st>>>(d);
+        k_dft_accum<32, RCH><<<grd, nt, 0, st>>>(d);
 }
 
 // ----------------------------------------------------------------- fluxes

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "nlf_internal.h"
+#include "dft_accum.cuh"
 
 namespace nlf {
 
@@ -98,35 +99,7 @@ __global__ void __launch_bounds__(128) k_accum_batch(const BatchDft a)
     }
     __syncthreads();
     if (f >= d.nf) return;
-    float ce[B], se[B], ch[B], sh[B];
-#pragma unroll
-    for (int s = 0; s < B; ++s) {
-        const float4 v = d.phase[s * d.nf + f];
-        ce[s] = v.x;
-        se[s] = v.y;
-        ch[s] = v.z;
-        sh[s] = v.w;
-    }
-    const int rmax = (int)min((long long)RCH, nr - r0);
-    for (int rr = 0; rr < rmax; ++rr) {
-        float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
-#pragma unroll
-        for (int s = 0; s < B; ++s) {
-            const float e = sEs[s][rr], h = sHs[s][rr];
-            er = fmaf(e, ce[s], er);
-            ei = fmaf(e, se[s], ei);
-            hr = fmaf(h, ch[s], hr);
-            hi = fmaf(h, sh[s], hi);
-        }
-        const long long o = (r0 + rr) * d.nf + f;
-        double2 ae = d.accE[o], ah = d.accH[o];
-        ae.x += (double)er;
-        ae.y += (double)ei;
-        ah.x += (double)hr;
-        ah.y += (double)hi;
-        d.accE[o] = ae;
-        d.accH[o] = ah;
-    }
+    accum_records<B, RCH>(d, r0, f, sEs, sHs);
 }
 
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st)

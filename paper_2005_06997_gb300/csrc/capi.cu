@@ -29,6 +29,9 @@ namespace nlf {
 void launch_step(const StepParams& p, cudaStream_t st);
 void launch_step_pml(const StepParams& p, cudaStream_t st);
 bool step_has_pml(const StepParams& p);
+long long tfsf_items(const StepParams& p);
+void launch_tfsf(const StepParams& p, cudaStream_t st);
+void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st);
 void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
 void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
@@ -770,6 +773,10 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
         nlf::launch_step(sp, st);
         c->launches += 1;
     }
+    if (nlf::tfsf_items(sp) > 0) {
+        nlf::launch_tfsf(sp, st);
+        c->launches += 1;
+    }
 }
 
 // One time step and its monitor work, launched on st.
@@ -860,6 +867,7 @@ struct BatchPlan {
     long long gnodes = 0;
     cudaStream_t cap = nullptr;
     bool any_pml = false;             // some instance has CPML tiles: second kernel on aux
+    long long tfsf_max = 0;           // largest TF/SF correction item count of an instance
     cudaStream_t aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     ~BatchPlan()
@@ -993,6 +1001,10 @@ long long plan_launch(BatchPlan* P, cudaStream_t st)
             nlf::launch_step_batch(bs, P->items, st);
             ++nodes;
         }
+        if (P->tfsf_max > 0) {
+            nlf::launch_tfsf_batch(bs, P->tfsf_max, st);
+            ++nodes;
+        }
         if (P->met_sites > 0) {
             nlf::launch_metal_batch(bs, P->met_sites, st);
             ++nodes;
@@ -1055,8 +1067,10 @@ BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
     P->K = act[0]->K;
     P->B = act[0]->B;
     P->U = act[0]->U;
-    for (nlf_ctx* x : act)
+    for (nlf_ctx* x : act) {
         if (nlf::step_has_pml(x->sp[0])) P->any_pml = true;
+        P->tfsf_max = std::max(P->tfsf_max, nlf::tfsf_items(x->sp[0]));
+    }
     if (P->any_pml) {
         if (cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess ||

@@ -13,9 +13,10 @@
 // operands by cp.async.  E, H and psi_H are double buffered (generation n
 // read, n+1 written), so tiles need no grid-wide barrier; every field crosses
 // HBM once per step apart from halos.  Tiles are classified once per block:
-// clear of the CPML slabs and of the TF/SF surface they run plain Yee
-// arithmetic with no per-cell tests; CPML tiles run in their own kernel
-// (more shared memory: the psi staging area) concurrently with the others.
+// clear of the CPML slabs they run plain Yee arithmetic with no per-cell
+// tests; CPML tiles run in their own kernel (more shared memory: the psi
+// staging area) concurrently with the others.  The TF/SF connection is a
+// separate small kernel (k_tfsf) of additive corrections on the TF surface.
 //
 // The material update (k_metal): one thread per material E-site of a
 // compact list rewrites E^{n+1} there from the H^{n+1/2} just written and
@@ -126,25 +127,11 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
 // two derivatives (used only inside the slab of that axis).  If own, store it
 // and its psi.
 //
-// TF: the incident plane wave (E_x, H_y along +z) is converted where an H
-// read crosses the TF surface: H_y on the planes k = lo_z - 1 and k = hi_z
-// and H_z on the planes j = lo_y - 1 and j = hi_y are scattered fields whose
-// E_x neighbour on the other side is a total field.
-template <int C, bool PML, bool TF>
+template <int C, bool PML>
 __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, float h0, float a_here, float a_next,
                                         float b_here, float b_next, bool own, float psA1 = 0.f, float psA2 = 0.f)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    if (TF) {
-        if (C == 1 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1]) {
-            if (c.k == p.tf_lo[2] - 1) a_next -= e_inc(p, p.tf_lo[2]);
-            if (c.k == p.tf_hi[2]) a_here -= e_inc(p, p.tf_hi[2]);
-        }
-        if (C == 2 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.k >= p.tf_lo[2] && c.k <= p.tf_hi[2]) {
-            if (c.j == p.tf_lo[1] - 1) b_next -= e_inc(p, c.k);
-            if (c.j == p.tf_hi[1]) b_here -= e_inc(p, c.k);
-        }
-    }
     float t1 = a_next - a_here;
     float t2 = b_next - b_here;
     if (PML) {
@@ -168,24 +155,12 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
 // E_C^{n+1} of the background at cell c from E^n = En and H^{n+1/2}:
 // hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2);
 // peA1, peA2: psi_E^n of the two derivatives (used only inside the slab).
-// TF: E_x on the planes k = lo_z and k = hi_z, and E_z on the planes
-// i = lo_x and i = hi_x, are total fields reading a scattered H_y.
 // Sites that hold a material are rewritten afterwards by k_metal.
-template <int C, bool PML, bool TF>
+template <int C, bool PML>
 __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float En, float hA2, float hA2m, float hA1,
                                        float hA1m, float peA1 = 0.f, float peA2 = 0.f)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    if (TF) {
-        if (C == 0 && c.i >= p.tf_lo[0] && c.i < p.tf_hi[0] && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1]) {
-            if (c.k == p.tf_lo[2]) hA1m += h_inc_next(p, p.tf_lo[2] - 1);
-            if (c.k == p.tf_hi[2]) hA1 += h_inc_next(p, p.tf_hi[2]);
-        }
-        if (C == 2 && c.j >= p.tf_lo[1] && c.j <= p.tf_hi[1] && c.k >= p.tf_lo[2] && c.k < p.tf_hi[2]) {
-            if (c.i == p.tf_lo[0]) hA2m += h_inc_next(p, c.k);
-            if (c.i == p.tf_hi[0]) hA2 += h_inc_next(p, c.k);
-        }
-    }
     float t1 = hA2 - hA2m;
     float t2 = hA1 - hA1m;
     if (PML) {
@@ -552,11 +527,10 @@ struct TmaRing {
     }
 };
 
-// The z march of one tile over planes [k0, k1).  Template classes, uniform
-// per block: PML = the tile or its halo reaches a CPML slab (psi arithmetic,
-// psi staged by cp.async); TF = it reaches the cells next to the TF/SF
-// surface (incident-field corrections).
-template <bool PML, bool TF, class SM>
+// The z march of one tile over planes [k0, k1).  PML (uniform per block):
+// the tile or its halo reaches a CPML slab (psi arithmetic, psi staged by
+// cp.async).
+template <bool PML, class SM>
 __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
 {
     constexpr int NE = SM::kNE, NH = SM::kNH;
@@ -596,9 +570,9 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
             if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
         }
-        hx_prev = h_cell<0, PML, TF>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
+        hx_prev = h_cell<0, PML>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
                                      r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2);
-        hy_prev = h_cell<1, PML, TF>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
+        hy_prev = h_cell<1, PML>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
                                      r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2);
     }
     if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
@@ -610,6 +584,13 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         const bool more = k + 1 < k1;
         r.wait_e(k + 1);
         r.wait_h(k);
+        // this plane's stages: E^n of planes k and k+1, H^{n-1/2} of plane k
+        const float* e0 = sm.sE[r.eslot(k)];
+        const float* e1 = sm.sE[r.eslot(k + 1)];
+        const float* h0 = sm.sHo[r.hslot(k)];
+        auto E0 = [&](int c, int y, int x) { return e0[(c * TMA_EY + y) * TMA_EX + x]; };
+        auto E1 = [&](int c, int y, int x) { return e1[(c * TMA_EY + y) * TMA_EX + x]; };
+        auto H0 = [&](int c, int y, int x) { return h0[(c * TMA_HY + y) * TMA_EX + x]; };
         const float* po = nullptr;
         const float* ph = nullptr;
         if constexpr (PML) {
@@ -635,44 +616,44 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         float hx = 0.f, hy = 0.f, hz = 0.f;
         float ex = 0.f, ey = 0.f, ez = 0.f;
         // f1: own H^{n+1/2}
-        if (in && !r.bad) {
+        if (in) {
             constexpr int S = BX * BY;
-            ex = r.e(k, 0, ly, lx);
-            ey = r.e(k, 1, ly, lx);
-            ez = r.e(k, 2, ly, lx);
-            hx = h_cell<0, PML, TF>(p, c, r.h(k, 0, ly, lx), ez, r.e(k, 2, ly + 1, lx), ey, r.e(k + 1, 1, ly, lx),
+            ex = E0(0, ly, lx);
+            ey = E0(1, ly, lx);
+            ez = E0(2, ly, lx);
+            hx = h_cell<0, PML>(p, c, H0(0, ly, lx), ez, E0(2, ly + 1, lx), ey, E1(1, ly, lx),
                                     true, PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f);
-            hy = h_cell<1, PML, TF>(p, c, r.h(k, 1, ly, lx), ex, r.e(k + 1, 0, ly, lx), ez, r.e(k, 2, ly, lx + 1),
+            hy = h_cell<1, PML>(p, c, H0(1, ly, lx), ex, E1(0, ly, lx), ez, E0(2, ly, lx + 1),
                                     true, PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f);
-            hz = h_cell<2, PML, TF>(p, c, r.h(k, 2, ly, lx), ey, r.e(k, 1, ly, lx + 1), ex, r.e(k, 0, ly + 1, lx),
+            hz = h_cell<2, PML>(p, c, H0(2, ly, lx), ey, E0(1, ly, lx + 1), ex, E0(0, ly + 1, lx),
                                     true, PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f);
             sH[0][ly][tx + 1] = hx;
             sH[1][ly][tx + 1] = hy;
             sH[2][ly][tx + 1] = hz;
         }
         // halo H on two warps: H_y, H_z at x0-1 (threads 0..BY-1), H_x, H_z at y0-1 (BY..BY+BX-1)
-        if (!r.bad) {
+        {
             constexpr int S = BX + BY;
             if (tid < BY) {
                 const int jh = y0 + tid, sy = tid + 1;
                 if (x0 > 0 && jh < p.ny) {
                     const Cell h = make_cell(p, x0 - 1, jh, k, PML);
-                    sH[1][sy][0] = h_cell<1, PML, TF>(p, h, r.h(k, 1, sy, 3), r.e(k, 0, sy, 3), r.e(k + 1, 0, sy, 3),
-                                                      r.e(k, 2, sy, 3), r.e(k, 2, sy, 4), false,
+                    sH[1][sy][0] = h_cell<1, PML>(p, h, H0(1, sy, 3), E0(0, sy, 3), E1(0, sy, 3),
+                                                      E0(2, sy, 3), E0(2, sy, 4), false,
                                                       PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                    sH[2][sy][0] = h_cell<2, PML, TF>(p, h, r.h(k, 2, sy, 3), r.e(k, 1, sy, 3), r.e(k, 1, sy, 4),
-                                                      r.e(k, 0, sy, 3), r.e(k, 0, sy + 1, 3), false,
+                    sH[2][sy][0] = h_cell<2, PML>(p, h, H0(2, sy, 3), E0(1, sy, 3), E0(1, sy, 4),
+                                                      E0(0, sy, 3), E0(0, sy + 1, 3), false,
                                                       PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
                 }
             } else if (tid < BY + BX) {
                 const int s0 = tid - BY, ih = x0 + s0, sx = s0 + 4;
                 if (y0 > 0 && ih < p.nx) {
                     const Cell h = make_cell(p, ih, y0 - 1, k, PML);
-                    sH[0][0][s0 + 1] = h_cell<0, PML, TF>(p, h, r.h(k, 0, 0, sx), r.e(k, 2, 0, sx), r.e(k, 2, 1, sx),
-                                                          r.e(k, 1, 0, sx), r.e(k + 1, 1, 0, sx), false,
+                    sH[0][0][s0 + 1] = h_cell<0, PML>(p, h, H0(0, 0, sx), E0(2, 0, sx), E0(2, 1, sx),
+                                                          E0(1, 0, sx), E1(1, 0, sx), false,
                                                           PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                    sH[2][0][s0 + 1] = h_cell<2, PML, TF>(p, h, r.h(k, 2, 0, sx), r.e(k, 1, 0, sx),
-                                                          r.e(k, 1, 0, sx + 1), r.e(k, 0, 0, sx), r.e(k, 0, 1, sx),
+                    sH[2][0][s0 + 1] = h_cell<2, PML>(p, h, H0(2, 0, sx), E0(1, 0, sx),
+                                                          E0(1, 0, sx + 1), E0(0, 0, sx), E0(0, 1, sx),
                                                           false, PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
                 }
             }
@@ -689,18 +670,18 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             const int ox = tx + 1;
             const float hzm = sH[2][ly - 1][ox], hzi = sH[2][ly][ox - 1];
             const float hyi = sH[1][ly][ox - 1], hxm = sH[0][ly - 1][ox];
-            if (PML || TF) {
+            if (PML) {
                 constexpr int S = BX * BY;
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML, TF>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
+                    e_cell<0, PML>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML, TF>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
+                    e_cell<1, PML>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML, TF>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
+                    e_cell<2, PML>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -721,30 +702,21 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     if constexpr (PML) cp_async_wait<0>();
 }
 
-// Classes of the box [lo, hi] (cells, inclusive): does it touch a CPML slab,
-// or a cell on which a TF/SF conversion happens (within one cell of the TF
-// surface)?
-__device__ __forceinline__ void tile_class(const StepParams& p, const int lo[3], const int hi[3], bool* pml,
-                                           bool* tf)
+// Does the box [lo, hi] (cells, inclusive) touch a CPML slab?
+__device__ __forceinline__ bool tile_in_pml(const StepParams& p, const int lo[3], const int hi[3])
 {
     const int n3[3] = {p.nx, p.ny, p.nz};
     bool b = false;
-    bool inner = true, outer = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a)
         if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) b = true;
-        // every conversion sits on the planes tf_lo - 1 .. tf_lo or tf_hi .. (tf_hi) of some axis
-        if (!(lo[a] > p.tf_lo[a] && hi[a] < p.tf_hi[a] - 1)) inner = false;
-        if (hi[a] < p.tf_lo[a] - 1 || lo[a] > p.tf_hi[a]) outer = true;
-    }
-    *pml = b;
-    *tf = p.tfsf && !inner && !outer;
+    return b;
 }
 
 
 // The single-grid step runs as two kernels over the same grid of tiles,
 // launched concurrently on two streams: k_step_pml takes the CPML tiles,
-// k_step the others (background and TF/SF), each block leaving at once if
+// k_step the others, each block leaving at once if
 // its tile belongs to the other kernel.  Without CPML tiles k_step alone runs.
 // Separate kernels let the background tiles run TMA-fed with fewer
 // registers and without the psi staging area: 5 blocks per SM instead of 4.
@@ -755,14 +727,7 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
     const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
-    bool pml, tf;
-    tile_class(p, lo, hi, &pml, &tf);
-    if (pml == PMLK) {
-        if (tf)
-            march_tma<PMLK, true>(p, x0, y0, k0, k1, sm);
-        else
-            march_tma<PMLK, false>(p, x0, y0, k0, k1, sm);
-    }
+    if (tile_in_pml(p, lo, hi) == PMLK) march_tma<PMLK>(p, x0, y0, k0, k1, sm);
     // the 1D incident grid and the step counter: block (0,0,0) of k_step
     if (!PMLK && bx == 0 && by == 0 && bz == 0) {
         const int tid = threadIdx.y * BX + threadIdx.x;
@@ -806,9 +771,148 @@ __device__ __forceinline__ int find_inst(const long long* end, int n, long long 
     return lo;
 }
 
+// ------------------------------------------------------------- TF/SF
+//
+// The total-field / scattered-field connection, applied after the EM step as
+// additive corrections.  The step kernels update every cell as if the grid
+// held one field; the TF/SF surface then needs H_y on the planes
+// k = lo_z - 1 and k = hi_z and H_z on the planes j = lo_y - 1 and j = hi_y
+// (scattered-field cells whose curl reads a total-field E_x) corrected by the
+// incident E_inc^n, and E_x on k = lo_z, hi_z and E_z on i = lo_x, hi_x
+// (total-field cells whose curl reads a scattered-field H) corrected by the
+// incident H_inc^{n+1/2}.  The update is linear, so E^{n+1} of every cell whose
+// curl reads a corrected H also receives Sb curl(dH); the cells so touched
+// are gathered here, each with its whole correction.  TF/SF cells lie outside
+// the CPML and the metal, so only the background coefficient Sb appears.
+//
+// Item sets (i in [lo_x, hi_x) unless stated, j/k ranges inclusive):
+//   0  E_x, j in [lo_y, hi_y], k in {lo_z-1, lo_z, hi_z, hi_z+1}
+//   1  E_x, j in {lo_y-1, lo_y, hi_y, hi_y+1}, k in [lo_z, hi_z] (not in set 0)
+//   2  E_y, i in {lo_x, hi_x}, j in {lo_y-1, hi_y}, k in [lo_z, hi_z]
+//   3  E_z, i in {lo_x, hi_x}, j in [lo_y, hi_y], k in [lo_z-1, hi_z]
+//   4  H_y, j in [lo_y, hi_y], k in {lo_z-1, hi_z}
+//   5  H_z, j in {lo_y-1, hi_y}, k in [lo_z, hi_z]
+// Sizes of the six item sets, in order.
+__host__ __device__ __forceinline__ void tfsf_sizes(const StepParams& p, long long n[6])
+{
+    const long long nx = p.tf_hi[0] - p.tf_lo[0], ny = p.tf_hi[1] - p.tf_lo[1] + 1,
+                    nz = p.tf_hi[2] - p.tf_lo[2] + 1;
+    n[0] = nx * ny * 4;
+    n[1] = nx * 4 * nz;
+    n[2] = 4 * nz;
+    n[3] = 2 * ny * (nz + 1);
+    n[4] = nx * ny * 2;
+    n[5] = nx * 2 * nz;
+}
+
+__host__ __device__ __forceinline__ long long tfsf_count(const StepParams& p)
+{
+    if (!p.tfsf) return 0;
+    long long n[6];
+    tfsf_sizes(p, n);
+    return n[0] + n[1] + n[2] + n[3] + n[4] + n[5];
+}
+
+__device__ __forceinline__ void tfsf_item(const StepParams& p, long long t)
+{
+    const int l0 = p.tf_lo[0], h0 = p.tf_hi[0], l1 = p.tf_lo[1], h1 = p.tf_hi[1], l2 = p.tf_lo[2],
+              h2 = p.tf_hi[2];
+    const int nx = h0 - l0, ny = h1 - l1 + 1;
+    long long n[6];
+    tfsf_sizes(p, n);
+    int set = 0;
+    long long r = t;
+    while (set < 6 && r >= n[set]) r -= n[set++];
+    if (set == 6) return;
+    const float S = p.S, Sb = p.Sb;
+    // dH_y on k = lo_z - 1, hi_z and dH_z on j = lo_y - 1, hi_y (plane k)
+    const float dy_lo = S * e_inc(p, l2), dy_hi = -S * e_inc(p, h2);
+    auto dz = [&](int jh, int k) { return (jh == l1 - 1 ? -S : S) * e_inc(p, k); };
+    int i, j, k, comp;
+    float v = 0.f;
+    bool isH = false;
+    if (set == 0 || set == 1) {
+        comp = 0;
+        i = l0 + (int)(r % nx);
+        r /= nx;
+        if (set == 0) {
+            j = l1 + (int)(r % ny);
+            const int kk[4] = {l2 - 1, l2, h2, h2 + 1};
+            k = kk[r / ny];
+        } else {
+            const int jj[4] = {l1 - 1, l1, h1, h1 + 1};
+            j = jj[r % 4];
+            k = l2 + (int)(r / 4);
+            if ((j == l1 || j == h1) && (k == l2 || k == h2)) return;   // in set 0
+        }
+        if (j >= l1 && j <= h1) {
+            if (k == l2 - 1) v -= Sb * dy_lo;
+            if (k == l2) v += Sb * dy_lo + Sb * h_inc_next(p, l2 - 1);
+            if (k == h2) v -= Sb * dy_hi + Sb * h_inc_next(p, h2);
+            if (k == h2 + 1) v += Sb * dy_hi;
+        }
+        if (k >= l2 && k <= h2) {
+            if (j == l1 - 1 || j == h1) v += Sb * dz(j, k);
+            if (j == l1) v -= Sb * dz(l1 - 1, k);
+            if (j == h1 + 1) v -= Sb * dz(h1, k);
+        }
+    } else if (set == 2) {
+        comp = 1;
+        i = (r & 1) ? h0 : l0;
+        j = (r & 2) ? h1 : l1 - 1;
+        k = l2 + (int)(r >> 2);
+        v = (i == l0 ? -Sb : Sb) * dz(j, k);
+    } else if (set == 3) {
+        comp = 2;
+        i = (r & 1) ? h0 : l0;
+        r >>= 1;
+        j = l1 + (int)(r % ny);
+        k = l2 - 1 + (int)(r / ny);
+        const float sg = i == l0 ? 1.f : -1.f;
+        if (k == l2 - 1) v += sg * Sb * dy_lo;
+        if (k == h2) v += sg * Sb * dy_hi;
+        if (k >= l2 && k < h2) v -= sg * Sb * h_inc_next(p, k);
+    } else if (set == 4) {
+        comp = 1;
+        isH = true;
+        i = l0 + (int)(r % nx);
+        r /= nx;
+        j = l1 + (int)(r % ny);
+        k = (r / ny) ? h2 : l2 - 1;
+        v = k == h2 ? dy_hi : dy_lo;
+    } else {
+        comp = 2;
+        isH = true;
+        i = l0 + (int)(r % nx);
+        r /= nx;
+        j = (r & 1) ? h1 : l1 - 1;
+        k = l2 + (int)(r >> 1);
+        v = dz(j, k);
+    }
+    const uint32_t q = ((uint32_t)k * p.ny + j) * p.px + i;
+    float* f = isH ? p.H1[comp] : p.E1[comp];
+    f[q] += v;
+}
+
+__global__ void __launch_bounds__(256) k_tfsf(const StepParams p, long long n)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) tfsf_item(p, t);
+}
+
+// Batched: block row y is instance y; items past that instance's count idle.
+__global__ void __launch_bounds__(256) k_tfsf_batch(const BatchStep a)
+{
+    const int q = blockIdx.y;
+    const StepParams& p = a.params[2 * q + (a.inst[q].base_par ^ a.launch_par)];
+    if (!p.tfsf) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < tfsf_count(p)) tfsf_item(p, t);
+}
+
 // Batched grids: one block per work item (instance, tile, z chunk) of the
 // concatenated list of every instance.  As for a single grid, two kernels
-// take the list concurrently, k_step_batch the background and TF/SF tiles
+// take the list concurrently, k_step_batch the background tiles
 // (TMA-fed) and k_step_batch_pml the CPML tiles, each block leaving at once if
 // its tile belongs to the other kernel.  A block stages its instance's
 // parameters in shared memory first.
@@ -919,6 +1023,19 @@ int step_kz(const StepParams& p)
 }
 
 bool step_has_pml(const StepParams& p) { return p.cpml[0] || p.cpml[1] || p.cpml[2]; }
+
+long long tfsf_items(const StepParams& p) { return tfsf_count(p); }
+
+void launch_tfsf(const StepParams& p, cudaStream_t st)
+{
+    const long long n = tfsf_count(p);
+    if (n > 0) k_tfsf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n);
+}
+
+void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st)
+{
+    if (max_items > 0) k_tfsf_batch<<<dim3((unsigned)((max_items + 255) / 256), (unsigned)a.n), 256, 0, st>>>(a);
+}
 
 void launch_step(const StepParams& p, cudaStream_t st)
 {
