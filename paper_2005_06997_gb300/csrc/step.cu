@@ -124,28 +124,27 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
 // ((curl E)_C = dE_{A2}/dx_{A1} - dE_{A1}/dx_{A2}, (C, A1, A2) cyclic):
 // a_here, a_next = E_{A2} at idx and idx + e_A1, b_here, b_next = E_{A1} at idx
 // and idx + e_A2 (zero beyond the wall).  psA1, psA2: psi_H^{n-1/2} of the
-// two derivatives (used only inside the slab of that axis).  If own, store it
-// and its psi.
+// two derivatives and pr1, pr2 the (b, c) CPML coefficients of their axes at
+// the cell (used only inside the slab of that axis).  If own, store it and
+// its psi.
 //
 template <int C, bool PML>
 __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, float h0, float a_here, float a_next,
-                                        float b_here, float b_next, bool own, float psA1 = 0.f, float psA2 = 0.f)
+                                        float b_here, float b_next, bool own, float psA1 = 0.f, float psA2 = 0.f,
+                                        float2 pr1 = {}, float2 pr2 = {})
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     float t1 = a_next - a_here;
     float t2 = b_next - b_here;
     if (PML) {
-        const int ix[3] = {c.i, c.j, c.k};
-        if (c.l[A1] >= 0) {
-            const float psi = __ldg(p.bH[A1] + ix[A1]) * psA1 + __ldg(p.cH[A1] + ix[A1]) * t1;
-            if (own) p.psiH1[A1][1][c.s[A1]] = psi;
-            t1 += psi;
-        }
-        if (c.l[A2] >= 0) {
-            const float psi = __ldg(p.bH[A2] + ix[A2]) * psA2 + __ldg(p.cH[A2] + ix[A2]) * t2;
-            if (own) p.psiH1[A2][0][c.s[A2]] = psi;
-            t2 += psi;
-        }
+        // pr = (b, c) of the derivative's axis at the cell; selects, not
+        // branches: lanes in and out of a slab take one path
+        const float psi1 = c.l[A1] >= 0 ? pr1.x * psA1 + pr1.y * t1 : 0.f;
+        const float psi2 = c.l[A2] >= 0 ? pr2.x * psA2 + pr2.y * t2 : 0.f;
+        if (own && c.l[A1] >= 0) p.psiH1[A1][1][c.s[A1]] = psi1;
+        if (own && c.l[A2] >= 0) p.psiH1[A2][0][c.s[A2]] = psi2;
+        t1 += psi1;
+        t2 += psi2;
     }
     const float h = h0 - p.S * (t1 - t2);
     if (own) p.H1[C][c.q] = h;
@@ -154,27 +153,24 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
 
 // E_C^{n+1} of the background at cell c from E^n = En and H^{n+1/2}:
 // hA2 = H_{A2}(idx), hA2m = H_{A2}(idx - e_A1), hA1 = H_{A1}(idx), hA1m = H_{A1}(idx - e_A2);
-// peA1, peA2: psi_E^n of the two derivatives (used only inside the slab).
+// peA1, peA2: psi_E^n of the two derivatives, pr1, pr2 the (b, c) of their
+// axes (used only inside the slab).
 // Sites that hold a material are rewritten afterwards by k_metal.
 template <int C, bool PML>
 __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float En, float hA2, float hA2m, float hA1,
-                                       float hA1m, float peA1 = 0.f, float peA2 = 0.f)
+                                       float hA1m, float peA1 = 0.f, float peA2 = 0.f, float2 pr1 = {},
+                                       float2 pr2 = {})
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     float t1 = hA2 - hA2m;
     float t2 = hA1 - hA1m;
     if (PML) {
-        const int ix[3] = {c.i, c.j, c.k};
-        if (c.l[A1] >= 0) {
-            const float psi = __ldg(p.bE[A1] + ix[A1]) * peA1 + __ldg(p.cE[A1] + ix[A1]) * t1;
-            p.psiE[A1][1][c.s[A1]] = psi;
-            t1 += psi;
-        }
-        if (c.l[A2] >= 0) {
-            const float psi = __ldg(p.bE[A2] + ix[A2]) * peA2 + __ldg(p.cE[A2] + ix[A2]) * t2;
-            p.psiE[A2][0][c.s[A2]] = psi;
-            t2 += psi;
-        }
+        const float psi1 = c.l[A1] >= 0 ? pr1.x * peA1 + pr1.y * t1 : 0.f;
+        const float psi2 = c.l[A2] >= 0 ? pr2.x * peA2 + pr2.y * t2 : 0.f;
+        if (c.l[A1] >= 0) p.psiE[A1][1][c.s[A1]] = psi1;
+        if (c.l[A2] >= 0) p.psiE[A2][0][c.s[A2]] = psi2;
+        t1 += psi1;
+        t2 += psi2;
     }
     p.E1[C][c.q] = En + p.Sb * (t1 - t2);
 }
@@ -313,16 +309,27 @@ __device__ void inc_step(const StepParams& p, int tid, int nt)
 // arrive off the critical path.  Per thread (own cell), by component C:
 // slot 2C / 2C+1 = psi_H^{n-1/2} of the A1 / A2 derivative, 6+2C / 7+2C the
 // same for psi_E^n; per halo thread, its two H components' A1 / A2 psi_H.
+// The tile's CPML coefficients (b_E, c_E, b_H, c_H) along x (x0-1 .. x0+BX-1)
+// and y (y0-1 .. y0+BY-1) sit beside them; those along z are uniform per
+// plane and read per plane.
 struct PsiShared {
     float own[2][12][BX * BY];
     float halo[2][4][BX + BY];
+    float cx[4][BX + 1];
+    float cy[4][BY + 1];
 };
 
-__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+// (b_E, c_E, b_H, c_H) of plane k along z.
+struct ZCoef {
+    float bE, cE, bH, cH;
+};
+
+__device__ __forceinline__ ZCoef zcoef(const StepParams& p, int k)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    const int kk = min(max(k, 0), p.nz - 1);
+    return ZCoef{__ldg(p.bE[2] + kk), __ldg(p.cE[2] + kk), __ldg(p.bH[2] + kk), __ldg(p.cH[2] + kk)};
 }
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
@@ -330,61 +337,140 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// 4-byte asynchronous copy; when !valid nothing is read and zero is written.
+__device__ __forceinline__ void cp_async4z(float* dst, const float* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// Slab geometry of one column (i, j) of a CPML tile, constant along z: the
+// slab positions along x and y and the z-independent parts of the psi
+// offsets (psi_x at ((k ny + j) 2L + l0), psi_y at ((k 2L + l1) nx + i),
+// psi_z at ((l2 ny + j) nx + i) for an L-cell CPML).
+struct PmlCol {
+    int l0, l1;
+    uint32_t s0b, s1b, s2b;
+};
+
+__device__ __forceinline__ PmlCol pml_col(const StepParams& p, int i, int j)
+{
+    PmlCol q;
+    q.l0 = slab_local(p, 0, i);
+    q.l1 = slab_local(p, 1, j);
+    const uint32_t two = 2u * (uint32_t)p.pml;
+    q.s0b = (uint32_t)j * two + (uint32_t)(q.l0 >= 0 ? q.l0 : 0);
+    q.s1b = (uint32_t)(q.l1 >= 0 ? q.l1 : 0) * (uint32_t)p.nx + (uint32_t)i;
+    q.s2b = (uint32_t)j * (uint32_t)p.nx + (uint32_t)i;
+    return q;
+}
+
+// Slab positions and psi offsets of cell (c.i, c.j, c.k) from its column;
+// the offset of an axis whose slab does not hold the cell is 0 (a valid
+// element that is never used).
+__device__ __forceinline__ void pml_cell(const StepParams& p, const PmlCol& q, Cell& c)
+{
+    const uint32_t two = 2u * (uint32_t)p.pml;
+    c.l[0] = q.l0;
+    c.l[1] = q.l1;
+    c.l[2] = slab_local(p, 2, c.k);
+    c.s[0] = q.l0 >= 0 ? q.s0b + (uint32_t)c.k * (uint32_t)p.ny * two : 0u;
+    c.s[1] = q.l1 >= 0 ? q.s1b + (uint32_t)c.k * two * (uint32_t)p.nx : 0u;
+    c.s[2] = c.l[2] >= 0 ? (uint32_t)c.l[2] * (uint32_t)p.ny * (uint32_t)p.nx + q.s2b : 0u;
+}
+
 // Queue the psi operands of component C at cell c: psi_H (d1, d2) and, if
-// dE, psi_E (e1, e2), for the derivatives whose slab holds the cell.
+// e1, psi_E (e1, e2); zero for a derivative whose slab does not hold the cell.
 template <int C>
 __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, float* d1, float* d2, float* e1,
                                           float* e2)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    if (c.l[A1] >= 0) {
-        cp_async4(d1, p.psiH0[A1][1] + c.s[A1]);
-        if (e1) cp_async4(e1, p.psiE[A1][1] + c.s[A1]);
+    if (p.cpml[A1]) {
+        const bool v = c.l[A1] >= 0;
+        cp_async4z(d1, p.psiH0[A1][1] + c.s[A1], v);
+        if (e1) cp_async4z(e1, p.psiE[A1][1] + c.s[A1], v);
     }
-    if (c.l[A2] >= 0) {
-        cp_async4(d2, p.psiH0[A2][0] + c.s[A2]);
-        if (e2) cp_async4(e2, p.psiE[A2][0] + c.s[A2]);
+    if (p.cpml[A2]) {
+        const bool v = c.l[A2] >= 0;
+        cp_async4z(d2, p.psiH0[A2][0] + c.s[A2], v);
+        if (e2) cp_async4z(e2, p.psiE[A2][0] + c.s[A2], v);
     }
 }
 
 // Queue every psi operand of plane kk into buffer b: own cell (i, j, kk) and,
-// for the halo threads, their halo H cell.
+// for the halo threads, their halo H cell (column geometry qh).
 __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, int b, int kk, int x0, int y0, int i,
-                                          int j, bool in, int slx, int sly, int tid)
+                                          int j, bool in, const PmlCol& qo, const PmlCol& qh, int tid)
 {
     if (in) {
         Cell c;
         c.i = i;
         c.j = j;
         c.k = kk;
-        c.l[0] = slx;
-        c.l[1] = sly;
-        c.l[2] = slab_local(p, 2, kk);
-        if (c.l[0] >= 0 || c.l[1] >= 0 || c.l[2] >= 0) {
-            cell_slabs(p, c);
-            float(*o)[BX * BY] = ps.own[b];
-            psi_fetch<0>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
-            psi_fetch<1>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
-            psi_fetch<2>(p, c, &o[4][tid], &o[5][tid], &o[10][tid], &o[11][tid]);
-        }
+        pml_cell(p, qo, c);
+        float(*o)[BX * BY] = ps.own[b];
+        psi_fetch<0>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
+        psi_fetch<1>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
+        psi_fetch<2>(p, c, &o[4][tid], &o[5][tid], &o[10][tid], &o[11][tid]);
     }
     float(*h)[BX + BY] = ps.halo[b];
     if (tid < BY) {
         const int jh = y0 + tid;
         if (x0 > 0 && jh < p.ny) {
-            const Cell c = make_cell(p, x0 - 1, jh, kk, true);
+            Cell c;
+            c.i = x0 - 1;
+            c.j = jh;
+            c.k = kk;
+            pml_cell(p, qh, c);
             psi_fetch<1>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
             psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
         }
     } else if (tid < BY + BX) {
         const int ih = x0 + tid - BY;
         if (y0 > 0 && ih < p.nx) {
-            const Cell c = make_cell(p, ih, y0 - 1, kk, true);
+            Cell c;
+            c.i = ih;
+            c.j = y0 - 1;
+            c.k = kk;
+            pml_cell(p, qh, c);
             psi_fetch<0>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
             psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
         }
     }
     cp_async_commit();
+}
+
+// (b, c) of axis a at a tile position: w = 0 for E, 2 for H; ux, uy the
+// offsets from (x0-1, y0-1); z from the plane's coefficients.
+template <int a>
+__device__ __forceinline__ float2 cpml_coef(const PsiShared& ps, int w, int ux, int uy, const ZCoef& z)
+{
+    if (a == 0) return make_float2(ps.cx[w][ux], ps.cx[w + 1][ux]);
+    if (a == 1) return make_float2(ps.cy[w][uy], ps.cy[w + 1][uy]);
+    return w == 0 ? make_float2(z.bE, z.cE) : make_float2(z.bH, z.cH);
+}
+
+// Fill the tile's coefficient tables (every thread of the block; a barrier
+// must follow before use).
+__device__ __forceinline__ void cpml_tables(const StepParams& p, PsiShared& ps, int x0, int y0, int tid)
+{
+    // the profile arrays are named member by member (no address of the
+    // parameter block is taken, which would move it to local memory)
+    auto tab = [&](int w, int a) -> const float* {
+        const float* e = w == 0 ? p.bE[a] : p.cE[a];
+        const float* h = w == 2 ? p.bH[a] : p.cH[a];
+        return w < 2 ? e : h;
+    };
+    for (int t = tid; t < 4 * (BX + 1); t += BX * BY) {
+        const int w = t / (BX + 1), u = t - w * (BX + 1);
+        ps.cx[w][u] = __ldg(tab(w, 0) + min(max(x0 - 1 + u, 0), p.nx - 1));
+    }
+    for (int t = tid; t < 4 * (BY + 1); t += BX * BY) {
+        const int w = t / (BY + 1), u = t - w * (BY + 1);
+        ps.cy[w][u] = __ldg(tab(w, 1) + min(max(y0 - 1 + u, 0), p.ny - 1));
+    }
 }
 
 // ------------------------------------------------------- TMA-fed z march
@@ -527,6 +613,15 @@ struct TmaRing {
     }
 };
 
+// (b, c) pairs of the A1 and A2 derivatives of component C (w = 0: E, 2: H).
+template <int C>
+__device__ __forceinline__ void cpml_pair(const PsiShared& ps, int w, int ux, int uy, const ZCoef& z, float2& pr1,
+                                          float2& pr2)
+{
+    pr1 = cpml_coef<(C + 1) % 3>(ps, w, ux, uy, z);
+    pr2 = cpml_coef<(C + 2) % 3>(ps, w, ux, uy, z);
+}
+
 // The z march of one tile over planes [k0, k1).  PML (uniform per block):
 // the tile or its halo reaches a CPML slab (psi arithmetic, psi staged by
 // cp.async).
@@ -538,8 +633,16 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
     const int lx = tx + 4, ly = ty + 1;               // own cell in an E or H stage
-    // slab positions of the own column (constant along z)
-    const int slx = PML ? slab_local(p, 0, i) : -1, sly = PML ? slab_local(p, 1, j) : -1;
+    // CPML geometry of the own column and of the halo column (constant along z)
+    PmlCol qo{}, qh{};
+    if constexpr (PML) {
+        qo = pml_col(p, i, j);
+        if (tid < BY)
+            qh = pml_col(p, x0 - 1, y0 + tid);
+        else if (tid < BY + BX)
+            qh = pml_col(p, x0 + tid - BY, y0 - 1);
+        cpml_tables(p, sm.ps, x0, y0, tid);
+    }
     TmaRing<SM> r{sm, p, k0, x0, y0};
     if (tid == 0) {
         for (int q = 0; q < NE; ++q) mbar_init(&sm.barE[q]);
@@ -560,22 +663,27 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     r.wait_e(k0 - 1);
     r.wait_e(k0);
     if (!r.bad && k0 > 0 && in) {
-        const Cell c = make_cell(p, i, j, k0 - 1, PML);
+        Cell c = make_cell(p, i, j, k0 - 1, false);
         const int pm = k0 - 1;
         // psi_H of H_x (A1 = y, A2 = z) and H_y (A1 = z, A2 = x) at plane k0-1
         float px1 = 0.f, px2 = 0.f, py1 = 0.f, py2 = 0.f;
-        if (PML) {
+        float2 cx1{}, cx2{}, cy1{}, cy2{};
+        if constexpr (PML) {
+            pml_cell(p, qo, c);
             if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
             if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
             if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
             if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
+            const ZCoef zp = zcoef(p, k0 - 1);
+            cpml_pair<0>(sm.ps, 2, tx + 1, ty + 1, zp, cx1, cx2);
+            cpml_pair<1>(sm.ps, 2, tx + 1, ty + 1, zp, cy1, cy2);
         }
         hx_prev = h_cell<0, PML>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
-                                     r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2);
+                                 r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2, cx1, cx2);
         hy_prev = h_cell<1, PML>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
-                                     r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2);
+                                 r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2, cy1, cy2);
     }
-    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, slx, sly, tid);
+    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid);
     bool fail = __syncthreads_or(r.bad);
     if (!fail && tid == 0 && k0 + NE - 1 <= k1) r.issue_e(k0 + NE - 1);
     int hb = 0, pb = 0;
@@ -596,7 +704,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         if constexpr (PML) {
             // psi of plane k+1 on its way while plane k is computed
             if (more) {
-                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, slx, sly, tid);
+                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, qo, qh, tid);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -609,24 +717,30 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         c.j = j;
         c.k = k;
         c.q = ((uint32_t)k * p.ny + j) * p.px + i;
-        c.l[0] = slx;
-        c.l[1] = sly;
-        c.l[2] = PML ? slab_local(p, 2, k) : -1;
-        if (PML) cell_slabs(p, c);
+        c.l[0] = c.l[1] = c.l[2] = -1;
+        if constexpr (PML) pml_cell(p, qo, c);
+        ZCoef uz{};
+        if constexpr (PML) uz = zcoef(p, k);      // plane k's coefficients along z
         float hx = 0.f, hy = 0.f, hz = 0.f;
         float ex = 0.f, ey = 0.f, ez = 0.f;
         // f1: own H^{n+1/2}
         if (in) {
             constexpr int S = BX * BY;
+            float2 c1{}, c2{}, d1{}, d2{}, e1{}, e2{};
+            if constexpr (PML) {
+                cpml_pair<0>(sm.ps, 2, tx + 1, ty + 1, uz, c1, c2);
+                cpml_pair<1>(sm.ps, 2, tx + 1, ty + 1, uz, d1, d2);
+                cpml_pair<2>(sm.ps, 2, tx + 1, ty + 1, uz, e1, e2);
+            }
             ex = E0(0, ly, lx);
             ey = E0(1, ly, lx);
             ez = E0(2, ly, lx);
-            hx = h_cell<0, PML>(p, c, H0(0, ly, lx), ez, E0(2, ly + 1, lx), ey, E1(1, ly, lx),
-                                    true, PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f);
-            hy = h_cell<1, PML>(p, c, H0(1, ly, lx), ex, E1(0, ly, lx), ez, E0(2, ly, lx + 1),
-                                    true, PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f);
-            hz = h_cell<2, PML>(p, c, H0(2, ly, lx), ey, E0(1, ly, lx + 1), ex, E0(0, ly + 1, lx),
-                                    true, PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f);
+            hx = h_cell<0, PML>(p, c, H0(0, ly, lx), ez, E0(2, ly + 1, lx), ey, E1(1, ly, lx), true,
+                                PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f, c1, c2);
+            hy = h_cell<1, PML>(p, c, H0(1, ly, lx), ex, E1(0, ly, lx), ez, E0(2, ly, lx + 1), true,
+                                PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f, d1, d2);
+            hz = h_cell<2, PML>(p, c, H0(2, ly, lx), ey, E0(1, ly, lx + 1), ex, E0(0, ly + 1, lx), true,
+                                PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f, e1, e2);
             sH[0][ly][tx + 1] = hx;
             sH[1][ly][tx + 1] = hy;
             sH[2][ly][tx + 1] = hz;
@@ -637,24 +751,36 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             if (tid < BY) {
                 const int jh = y0 + tid, sy = tid + 1;
                 if (x0 > 0 && jh < p.ny) {
-                    const Cell h = make_cell(p, x0 - 1, jh, k, PML);
-                    sH[1][sy][0] = h_cell<1, PML>(p, h, H0(1, sy, 3), E0(0, sy, 3), E1(0, sy, 3),
-                                                      E0(2, sy, 3), E0(2, sy, 4), false,
-                                                      PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                    sH[2][sy][0] = h_cell<2, PML>(p, h, H0(2, sy, 3), E0(1, sy, 3), E0(1, sy, 4),
-                                                      E0(0, sy, 3), E0(0, sy + 1, 3), false,
-                                                      PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
+                    Cell h = make_cell(p, x0 - 1, jh, k, false);
+                    float2 c1{}, c2{}, d1{}, d2{};
+                    if constexpr (PML) {
+                        pml_cell(p, qh, h);
+                        cpml_pair<1>(sm.ps, 2, 0, sy, uz, c1, c2);
+                        cpml_pair<2>(sm.ps, 2, 0, sy, uz, d1, d2);
+                    }
+                    sH[1][sy][0] = h_cell<1, PML>(p, h, H0(1, sy, 3), E0(0, sy, 3), E1(0, sy, 3), E0(2, sy, 3),
+                                                  E0(2, sy, 4), false, PML ? ph[0 * S] : 0.f,
+                                                  PML ? ph[1 * S] : 0.f, c1, c2);
+                    sH[2][sy][0] = h_cell<2, PML>(p, h, H0(2, sy, 3), E0(1, sy, 3), E0(1, sy, 4), E0(0, sy, 3),
+                                                  E0(0, sy + 1, 3), false, PML ? ph[2 * S] : 0.f,
+                                                  PML ? ph[3 * S] : 0.f, d1, d2);
                 }
             } else if (tid < BY + BX) {
                 const int s0 = tid - BY, ih = x0 + s0, sx = s0 + 4;
                 if (y0 > 0 && ih < p.nx) {
-                    const Cell h = make_cell(p, ih, y0 - 1, k, PML);
+                    Cell h = make_cell(p, ih, y0 - 1, k, false);
+                    float2 c1{}, c2{}, d1{}, d2{};
+                    if constexpr (PML) {
+                        pml_cell(p, qh, h);
+                        cpml_pair<0>(sm.ps, 2, s0 + 1, 0, uz, c1, c2);
+                        cpml_pair<2>(sm.ps, 2, s0 + 1, 0, uz, d1, d2);
+                    }
                     sH[0][0][s0 + 1] = h_cell<0, PML>(p, h, H0(0, 0, sx), E0(2, 0, sx), E0(2, 1, sx),
-                                                          E0(1, 0, sx), E1(1, 0, sx), false,
-                                                          PML ? ph[0 * S] : 0.f, PML ? ph[1 * S] : 0.f);
-                    sH[2][0][s0 + 1] = h_cell<2, PML>(p, h, H0(2, 0, sx), E0(1, 0, sx),
-                                                          E0(1, 0, sx + 1), E0(0, 0, sx), E0(0, 1, sx),
-                                                          false, PML ? ph[2 * S] : 0.f, PML ? ph[3 * S] : 0.f);
+                                                      E0(1, 0, sx), E1(1, 0, sx), false, PML ? ph[0 * S] : 0.f,
+                                                      PML ? ph[1 * S] : 0.f, c1, c2);
+                    sH[2][0][s0 + 1] = h_cell<2, PML>(p, h, H0(2, 0, sx), E0(1, 0, sx), E0(1, 0, sx + 1),
+                                                      E0(0, 0, sx), E0(0, 1, sx), false, PML ? ph[2 * S] : 0.f,
+                                                      PML ? ph[3 * S] : 0.f, d1, d2);
                 }
             }
         }
@@ -672,16 +798,25 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             const float hyi = sH[1][ly][ox - 1], hxm = sH[0][ly - 1][ox];
             if (PML) {
                 constexpr int S = BX * BY;
+                float2 c1{}, c2{}, d1{}, d2{}, e1{}, e2{};
+                if constexpr (PML) {
+                    cpml_pair<0>(sm.ps, 0, tx + 1, ty + 1, uz, c1, c2);
+                    cpml_pair<1>(sm.ps, 0, tx + 1, ty + 1, uz, d1, d2);
+                    cpml_pair<2>(sm.ps, 0, tx + 1, ty + 1, uz, e1, e2);
+                }
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f);
+                    e_cell<0, PML>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f,
+                                   c1, c2);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f);
+                    e_cell<1, PML>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f,
+                                   d1, d2);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f);
+                    e_cell<2, PML>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f,
+                                   e1, e2);
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
@@ -738,6 +873,9 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
 
 using SharedBG = TileSharedTMA<NE_STAGE, NH_STAGE, false>;
 using SharedPML = TileSharedTMA<NE_PML, NH_PML, true>;
+// PML_BLOCKS blocks of the CPML kernel (plus the 1 KB the SM reserves per
+// block) must fit the SM's 228 KB of shared memory
+static_assert(PML_BLOCKS * (sizeof(SharedPML) + 128 + 1024) <= 228 * 1024, "CPML tile blocks do not fit an SM");
 
 __global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
 {
