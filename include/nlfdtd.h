@@ -155,9 +155,10 @@ typedef struct {
     double step_kernel_bytes;     /* EM step kernel: 48 cells + 32 pml_slab_cells (E and H read
                                    * and written once, per slab cell and axis two psi_E read and
                                    * written, two psi_H read and written) */
-    double metal_kernel_bytes;    /* material update: 17 material_sites (site entry 4, id 1, E read
-                                   * and written 8, H 4) + 8 (2 + gnor) metal_sites (P_f, a_f and
-                                   * the GNOR history read and written) + 16 n_poles pole_sites */
+    double metal_kernel_bytes;    /* material update: 21 material_sites (site entry and cell offset
+                                   * 8, id 1, E read and written 8, H 4) + 8 (2 + gnor) metal_sites
+                                   * (P_f, a_f and the GNOR history read and written)
+                                   * + 16 n_poles pole_sites */
     long long material_sites;     /* E-sites holding any material (entries of the site list) */
     double dt;                    /* s */
     int gnor, n_poles;

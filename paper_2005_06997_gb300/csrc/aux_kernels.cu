@@ -60,8 +60,8 @@ __global__ void k_voxelise(const VoxParams v)
 // (component << 30) | box offset.  Each warp reserves its run with one atomic,
 // so runs land in any order while each run keeps box order; the material
 // update is independent per site, so the order does not change any result.
-__global__ void k_site_list(const uint8_t* __restrict__ mat, long long n3, uint32_t* sites, long long nb,
-                            unsigned long long* count)
+__global__ void k_site_list(const uint8_t* __restrict__ mat, long long n3, uint32_t* sites, uint32_t* site_q,
+                            long long nb, SiteGeom g, unsigned long long* count)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool has = t < n3 && mat[t] != 0;
@@ -74,14 +74,21 @@ __global__ void k_site_list(const uint8_t* __restrict__ mat, long long n3, uint3
     if (has) {
         const uint32_t c = (uint32_t)(t / nb);
         const uint32_t b = (uint32_t)(t - (long long)c * nb);
-        sites[base + __popc(mask & ((1u << lane) - 1u))] = (c << 30) | b;
+        const uint32_t bi = b % (uint32_t)g.bb_n[0], r = b / (uint32_t)g.bb_n[0];
+        const uint32_t bj = r % (uint32_t)g.bb_n[1], bk = r / (uint32_t)g.bb_n[1];
+        const unsigned long long w = base + __popc(mask & ((1u << lane) - 1u));
+        sites[w] = (c << 30) | b;
+        site_q[w] = ((uint32_t)(g.bb_lo[2] + (int)bk) * (uint32_t)g.ny + (uint32_t)(g.bb_lo[1] + (int)bj)) *
+                        (uint32_t)g.px +
+                    (uint32_t)(g.bb_lo[0] + (int)bi);
     }
 }
 
-void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st)
+void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, uint32_t* site_q, const SiteGeom& g,
+                      unsigned long long* count, cudaStream_t st)
 {
     const long long n = 3 * nb;
-    k_site_list<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mat, n, sites, nb, count);
+    k_site_list<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mat, n, sites, site_q, nb, g, count);
 }
 
 void launch_voxelise(const VoxParams& v, cudaStream_t st)

@@ -33,7 +33,8 @@ long long tfsf_items(const StepParams& p);
 void launch_tfsf(const StepParams& p, cudaStream_t st);
 void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st);
 void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
-void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, unsigned long long* count, cudaStream_t st);
+void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, uint32_t* site_q, const SiteGeom& g,
+                      unsigned long long* count, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
 void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
                        int slot, const long long* step, int* err, cudaStream_t st);
@@ -108,7 +109,7 @@ struct nlf_ctx {
     size_t off_psiE[3] = {0, 0, 0}, off_psiH[2][3] = {{0, 0, 0}, {0, 0, 0}};
     size_t off_prof[3] = {0, 0, 0};
     size_t off_inc = 0;
-    size_t off_sites = 0;
+    size_t off_sites = 0, off_siteq = 0;
     size_t off_mat = 0, off_P[2] = {0, 0}, off_auxf = 0, off_gdp = 0, off_pcp = 0, off_auxcp = 0, off_coef = 0,
            off_free = 0, off_counts = 0;
     size_t off_rec = 0, off_dcoef = 0, off_omega = 0, off_samples = 0, off_sstep = 0, off_phase = 0, off_acc = 0,
@@ -414,6 +415,7 @@ int plan(nlf_ctx* c)
         const size_t nb = (size_t)c->nbb;
         c->off_mat = take(3 * nb);
         c->off_sites = take(3 * nb * sizeof(uint32_t));
+        c->off_siteq = take(3 * nb * sizeof(uint32_t));
         c->off_P[0] = take(3 * nb * sizeof(float));
         c->off_P[1] = take(3 * nb * sizeof(float));
         c->off_auxf = take(3 * nb * sizeof(float));
@@ -551,6 +553,7 @@ void fill_params(nlf_ctx* c)
             for (int k = 0; k < 3; ++k) {
                 p.mat[k] = at<uint8_t>(c, c->off_mat) + k * nb;
                 p.sites = at<uint32_t>(c, c->off_sites);
+                p.site_q = at<uint32_t>(c, c->off_siteq);
                 p.P0[k] = at<float>(c, c->off_P[r]) + k * nb;
                 p.P1[k] = at<float>(c, c->off_P[w]) + k * nb;
                 p.auxf[k] = at<float>(c, c->off_auxf) + k * nb;
@@ -700,7 +703,15 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         if ((rc = put(c->off_omega, c->omega.data(), c->omega.size() * sizeof(double)))) return rc;
     }
     if (c->has_metal) {
+        nlf::SiteGeom sg{};
+        for (int a = 0; a < 3; ++a) {
+            sg.bb_lo[a] = c->bb_lo[a];
+            sg.bb_n[a] = c->bb_n[a];
+        }
+        sg.ny = c->g.ny;
+        sg.px = c->px;
         nlf::launch_site_list(at<uint8_t>(c, c->off_mat), c->nbb, at<uint32_t>(c, c->off_sites),
+                              at<uint32_t>(c, c->off_siteq), sg,
                               at<unsigned long long>(c, c->off_counts) + 3, st);
         CK(cudaGetLastError());
         c->launches += 1;
@@ -724,7 +735,7 @@ int initialise(nlf_ctx* c, cudaStream_t st)
     in.n_poles = c->max_poles;
     in.material_sites = c->n_msites;
     in.step_kernel_bytes = 48.0 * c->ncell + 32.0 * in.pml_slab_cells;
-    in.metal_kernel_bytes = 17.0 * c->n_msites + 8.0 * (2 + (c->any_gnor ? 1 : 0)) * in.metal_sites +
+    in.metal_kernel_bytes = 21.0 * c->n_msites + 8.0 * (2 + (c->any_gnor ? 1 : 0)) * in.metal_sites +
                             16.0 * c->max_poles * in.pole_sites;
     in.step_bytes = in.step_kernel_bytes + in.metal_kernel_bytes;
     c->ready = true;

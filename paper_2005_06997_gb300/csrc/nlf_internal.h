@@ -100,6 +100,7 @@ struct StepParams {
     int bb_lo[3], bb_n[3];
     const uint8_t* mat[3];
     const uint32_t* sites;      // material E-sites of the box: (component << 30) | box offset
+    const uint32_t* site_q;     // their cell offsets in the field arrays
     const MatCoef* coef;        // [n_materials + 1], index 0 unused
     const float* P0[3];
     float* P1[3];
@@ -123,6 +124,12 @@ struct VoxParams {
     uint8_t* mat[3];
     unsigned long long* counts;   // [3] plasmonic E-sites per component (atomic)
     const int* free_e;            // [NLF_MAX_MAT + 1] material has free electrons
+};
+
+// Where the metal box sits in the field arrays (for the site list).
+struct SiteGeom {
+    int bb_lo[3], bb_n[3];
+    int ny, px;
 };
 
 struct DftParams {

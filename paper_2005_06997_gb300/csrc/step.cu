@@ -190,14 +190,11 @@ __device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint3
 // the material's coefficients are consulted, so one memory round trip serves
 // the whole site; arrays a material does not use are read and ignored.
 template <int C>
-__device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b)
+__device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint32_t q)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
-    const uint32_t bk = b / sz, r = b - bk * sz, bj = r / sy, bi = r - bj * sy;
     const uint32_t st[3] = {1u, (uint32_t)p.px, (uint32_t)p.px * (uint32_t)p.ny};
-    const uint32_t q = (uint32_t)(p.bb_lo[2] + (int)bk) * st[2] + (uint32_t)(p.bb_lo[1] + (int)bj) * st[1] +
-                       (uint32_t)(p.bb_lo[0] + (int)bi);
     const int id = __ldg(p.mat[C] + b);
     const float h2 = p.H1[A2][q], h2m = p.H1[A2][q - st[A1]];
     const float h1 = p.H1[A1][q], h1m = p.H1[A1][q - st[A2]];
@@ -245,22 +242,23 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b)
     }
 }
 
-// Entry e of the material site list.
-__device__ __forceinline__ void metal_entry(const StepParams& p, uint32_t e)
+// Entry t of the material site list (box entry e, cell offset q).
+__device__ __forceinline__ void metal_entry(const StepParams& p, long long t)
 {
+    const uint32_t e = __ldg(p.sites + t), q = __ldg(p.site_q + t);
     const uint32_t c = e >> 30, b = e & 0x3fffffffu;
     if (c == 0)
-        metal_site<0>(p, b);
+        metal_site<0>(p, b, q);
     else if (c == 1)
-        metal_site<1>(p, b);
+        metal_site<1>(p, b, q);
     else
-        metal_site<2>(p, b);
+        metal_site<2>(p, b, q);
 }
 
 __global__ void __launch_bounds__(256) k_metal(const StepParams p, long long n_sites)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_sites) metal_entry(p, __ldg(p.sites + t));
+    if (t < n_sites) metal_entry(p, t);
 }
 
 __device__ double source_value(const StepParams& p, double t)
@@ -1134,7 +1132,7 @@ __global__ void __launch_bounds__(256) k_metal_batch(const BatchStep a)
          w += (long long)gridDim.x * blockDim.x) {
         const int q = find_inst(s_end, a.n, w);
         const StepParams& p = a.params[2 * q + (a.inst[q].base_par ^ a.launch_par)];
-        metal_entry(p, __ldg(p.sites + (w - (q > 0 ? s_end[q - 1] : 0))));
+        metal_entry(p, w - (q > 0 ? s_end[q - 1] : 0));
     }
 }
 
