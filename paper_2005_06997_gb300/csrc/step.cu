@@ -128,7 +128,7 @@ __device__ __forceinline__ Cell make_cell(const StepParams& p, int i, int j, int
 // the cell (used only inside the slab of that axis).  If own, store it and
 // its psi.
 //
-template <int C, bool PML>
+template <int C, bool PML, int AX = 7>
 __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, float h0, float a_here, float a_next,
                                         float b_here, float b_next, bool own, float psA1 = 0.f, float psA2 = 0.f,
                                         float2 pr1 = {}, float2 pr2 = {})
@@ -139,12 +139,17 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
     if (PML) {
         // pr = (b, c) of the derivative's axis at the cell; selects, not
         // branches: lanes in and out of a slab take one path
-        const float psi1 = c.l[A1] >= 0 ? pr1.x * psA1 + pr1.y * t1 : 0.f;
-        const float psi2 = c.l[A2] >= 0 ? pr2.x * psA2 + pr2.y * t2 : 0.f;
-        if (own && c.l[A1] >= 0) p.psiH1[A1][1][c.s[A1]] = psi1;
-        if (own && c.l[A2] >= 0) p.psiH1[A2][0][c.s[A2]] = psi2;
-        t1 += psi1;
-        t2 += psi2;
+        // AX: the slab axes the tile touches (compile time); others have no psi here
+        if (AX >> A1 & 1) {
+            const float psi1 = c.l[A1] >= 0 ? pr1.x * psA1 + pr1.y * t1 : 0.f;
+            if (own && c.l[A1] >= 0) p.psiH1[A1][1][c.s[A1]] = psi1;
+            t1 += psi1;
+        }
+        if (AX >> A2 & 1) {
+            const float psi2 = c.l[A2] >= 0 ? pr2.x * psA2 + pr2.y * t2 : 0.f;
+            if (own && c.l[A2] >= 0) p.psiH1[A2][0][c.s[A2]] = psi2;
+            t2 += psi2;
+        }
     }
     const float h = h0 - p.S * (t1 - t2);
     if (own) p.H1[C][c.q] = h;
@@ -156,7 +161,7 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
 // peA1, peA2: psi_E^n of the two derivatives, pr1, pr2 the (b, c) of their
 // axes (used only inside the slab).
 // Sites that hold a material are rewritten afterwards by k_metal.
-template <int C, bool PML>
+template <int C, bool PML, int AX = 7>
 __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float En, float hA2, float hA2m, float hA1,
                                        float hA1m, float peA1 = 0.f, float peA2 = 0.f, float2 pr1 = {},
                                        float2 pr2 = {})
@@ -165,12 +170,16 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float
     float t1 = hA2 - hA2m;
     float t2 = hA1 - hA1m;
     if (PML) {
-        const float psi1 = c.l[A1] >= 0 ? pr1.x * peA1 + pr1.y * t1 : 0.f;
-        const float psi2 = c.l[A2] >= 0 ? pr2.x * peA2 + pr2.y * t2 : 0.f;
-        if (c.l[A1] >= 0) p.psiE[A1][1][c.s[A1]] = psi1;
-        if (c.l[A2] >= 0) p.psiE[A2][0][c.s[A2]] = psi2;
-        t1 += psi1;
-        t2 += psi2;
+        if (AX >> A1 & 1) {
+            const float psi1 = c.l[A1] >= 0 ? pr1.x * peA1 + pr1.y * t1 : 0.f;
+            if (c.l[A1] >= 0) p.psiE[A1][1][c.s[A1]] = psi1;
+            t1 += psi1;
+        }
+        if (AX >> A2 & 1) {
+            const float psi2 = c.l[A2] >= 0 ? pr2.x * peA2 + pr2.y * t2 : 0.f;
+            if (c.l[A2] >= 0) p.psiE[A2][0][c.s[A2]] = psi2;
+            t2 += psi2;
+        }
     }
     p.E1[C][c.q] = En + p.Sb * (t1 - t2);
 }
@@ -380,17 +389,17 @@ __device__ __forceinline__ void pml_cell(const StepParams& p, const PmlCol& q, C
 
 // Queue the psi operands of component C at cell c: psi_H (d1, d2) and, if
 // e1, psi_E (e1, e2); zero for a derivative whose slab does not hold the cell.
-template <int C>
+template <int C, int AX>
 __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, float* d1, float* d2, float* e1,
                                           float* e2)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    if (p.cpml[A1]) {
+    if ((AX >> A1 & 1) && p.cpml[A1]) {
         const bool v = c.l[A1] >= 0;
         cp_async4z(d1, p.psiH0[A1][1] + c.s[A1], v);
         if (e1) cp_async4z(e1, p.psiE[A1][1] + c.s[A1], v);
     }
-    if (p.cpml[A2]) {
+    if ((AX >> A2 & 1) && p.cpml[A2]) {
         const bool v = c.l[A2] >= 0;
         cp_async4z(d2, p.psiH0[A2][0] + c.s[A2], v);
         if (e2) cp_async4z(e2, p.psiE[A2][0] + c.s[A2], v);
@@ -399,6 +408,7 @@ __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, fl
 
 // Queue every psi operand of plane kk into buffer b: own cell (i, j, kk) and,
 // for the halo threads, their halo H cell (column geometry qh).
+template <int AX>
 __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, int b, int kk, int x0, int y0, int i,
                                           int j, bool in, const PmlCol& qo, const PmlCol& qh, int tid)
 {
@@ -409,9 +419,9 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
         c.k = kk;
         pml_cell(p, qo, c);
         float(*o)[BX * BY] = ps.own[b];
-        psi_fetch<0>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
-        psi_fetch<1>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
-        psi_fetch<2>(p, c, &o[4][tid], &o[5][tid], &o[10][tid], &o[11][tid]);
+        psi_fetch<0, AX>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
+        psi_fetch<1, AX>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
+        psi_fetch<2, AX>(p, c, &o[4][tid], &o[5][tid], &o[10][tid], &o[11][tid]);
     }
     float(*h)[BX + BY] = ps.halo[b];
     if (tid < BY) {
@@ -422,8 +432,8 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
             c.j = jh;
             c.k = kk;
             pml_cell(p, qh, c);
-            psi_fetch<1>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
-            psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
+            psi_fetch<1, AX>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
+            psi_fetch<2, AX>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
         }
     } else if (tid < BY + BX) {
         const int ih = x0 + tid - BY;
@@ -433,8 +443,8 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
             c.j = y0 - 1;
             c.k = kk;
             pml_cell(p, qh, c);
-            psi_fetch<0>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
-            psi_fetch<2>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
+            psi_fetch<0, AX>(p, c, &h[0][tid], &h[1][tid], nullptr, nullptr);
+            psi_fetch<2, AX>(p, c, &h[2][tid], &h[3][tid], nullptr, nullptr);
         }
     }
     cp_async_commit();
@@ -623,7 +633,7 @@ __device__ __forceinline__ void cpml_pair(const PsiShared& ps, int w, int ux, in
 // The z march of one tile over planes [k0, k1).  PML (uniform per block):
 // the tile or its halo reaches a CPML slab (psi arithmetic, psi staged by
 // cp.async).
-template <bool PML, class SM>
+template <bool PML, int AX, class SM>
 __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
 {
     constexpr int NE = SM::kNE, NH = SM::kNH;
@@ -676,12 +686,12 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             cpml_pair<0>(sm.ps, 2, tx + 1, ty + 1, zp, cx1, cx2);
             cpml_pair<1>(sm.ps, 2, tx + 1, ty + 1, zp, cy1, cy2);
         }
-        hx_prev = h_cell<0, PML>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
+        hx_prev = h_cell<0, PML, AX>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
                                  r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2, cx1, cx2);
-        hy_prev = h_cell<1, PML>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
+        hy_prev = h_cell<1, PML, AX>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
                                  r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2, cy1, cy2);
     }
-    if constexpr (PML) psi_plane(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid);
+    if constexpr (PML) psi_plane<AX>(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid);
     bool fail = __syncthreads_or(r.bad);
     if (!fail && tid == 0 && k0 + NE - 1 <= k1) r.issue_e(k0 + NE - 1);
     int hb = 0, pb = 0;
@@ -702,7 +712,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         if constexpr (PML) {
             // psi of plane k+1 on its way while plane k is computed
             if (more) {
-                psi_plane(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, qo, qh, tid);
+                psi_plane<AX>(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, qo, qh, tid);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -733,11 +743,11 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
             ex = E0(0, ly, lx);
             ey = E0(1, ly, lx);
             ez = E0(2, ly, lx);
-            hx = h_cell<0, PML>(p, c, H0(0, ly, lx), ez, E0(2, ly + 1, lx), ey, E1(1, ly, lx), true,
+            hx = h_cell<0, PML, AX>(p, c, H0(0, ly, lx), ez, E0(2, ly + 1, lx), ey, E1(1, ly, lx), true,
                                 PML ? po[0 * S] : 0.f, PML ? po[1 * S] : 0.f, c1, c2);
-            hy = h_cell<1, PML>(p, c, H0(1, ly, lx), ex, E1(0, ly, lx), ez, E0(2, ly, lx + 1), true,
+            hy = h_cell<1, PML, AX>(p, c, H0(1, ly, lx), ex, E1(0, ly, lx), ez, E0(2, ly, lx + 1), true,
                                 PML ? po[2 * S] : 0.f, PML ? po[3 * S] : 0.f, d1, d2);
-            hz = h_cell<2, PML>(p, c, H0(2, ly, lx), ey, E0(1, ly, lx + 1), ex, E0(0, ly + 1, lx), true,
+            hz = h_cell<2, PML, AX>(p, c, H0(2, ly, lx), ey, E0(1, ly, lx + 1), ex, E0(0, ly + 1, lx), true,
                                 PML ? po[4 * S] : 0.f, PML ? po[5 * S] : 0.f, e1, e2);
             sH[0][ly][tx + 1] = hx;
             sH[1][ly][tx + 1] = hy;
@@ -756,10 +766,10 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                         cpml_pair<1>(sm.ps, 2, 0, sy, uz, c1, c2);
                         cpml_pair<2>(sm.ps, 2, 0, sy, uz, d1, d2);
                     }
-                    sH[1][sy][0] = h_cell<1, PML>(p, h, H0(1, sy, 3), E0(0, sy, 3), E1(0, sy, 3), E0(2, sy, 3),
+                    sH[1][sy][0] = h_cell<1, PML, AX>(p, h, H0(1, sy, 3), E0(0, sy, 3), E1(0, sy, 3), E0(2, sy, 3),
                                                   E0(2, sy, 4), false, PML ? ph[0 * S] : 0.f,
                                                   PML ? ph[1 * S] : 0.f, c1, c2);
-                    sH[2][sy][0] = h_cell<2, PML>(p, h, H0(2, sy, 3), E0(1, sy, 3), E0(1, sy, 4), E0(0, sy, 3),
+                    sH[2][sy][0] = h_cell<2, PML, AX>(p, h, H0(2, sy, 3), E0(1, sy, 3), E0(1, sy, 4), E0(0, sy, 3),
                                                   E0(0, sy + 1, 3), false, PML ? ph[2 * S] : 0.f,
                                                   PML ? ph[3 * S] : 0.f, d1, d2);
                 }
@@ -773,10 +783,10 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                         cpml_pair<0>(sm.ps, 2, s0 + 1, 0, uz, c1, c2);
                         cpml_pair<2>(sm.ps, 2, s0 + 1, 0, uz, d1, d2);
                     }
-                    sH[0][0][s0 + 1] = h_cell<0, PML>(p, h, H0(0, 0, sx), E0(2, 0, sx), E0(2, 1, sx),
+                    sH[0][0][s0 + 1] = h_cell<0, PML, AX>(p, h, H0(0, 0, sx), E0(2, 0, sx), E0(2, 1, sx),
                                                       E0(1, 0, sx), E1(1, 0, sx), false, PML ? ph[0 * S] : 0.f,
                                                       PML ? ph[1 * S] : 0.f, c1, c2);
-                    sH[2][0][s0 + 1] = h_cell<2, PML>(p, h, H0(2, 0, sx), E0(1, 0, sx), E0(1, 0, sx + 1),
+                    sH[2][0][s0 + 1] = h_cell<2, PML, AX>(p, h, H0(2, 0, sx), E0(1, 0, sx), E0(1, 0, sx + 1),
                                                       E0(0, 0, sx), E0(0, 1, sx), false, PML ? ph[2 * S] : 0.f,
                                                       PML ? ph[3 * S] : 0.f, d1, d2);
                 }
@@ -803,17 +813,17 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                     cpml_pair<2>(sm.ps, 0, tx + 1, ty + 1, uz, e1, e2);
                 }
                 if (j >= 1 && k >= 1)
-                    e_cell<0, PML>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f,
+                    e_cell<0, PML, AX>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f,
                                    c1, c2);
                 else
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
-                    e_cell<1, PML>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f,
+                    e_cell<1, PML, AX>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f,
                                    d1, d2);
                 else
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
-                    e_cell<2, PML>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f,
+                    e_cell<2, PML, AX>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f,
                                    e1, e2);
                 else
                     p.E1[2][c.q] = 0.f;
@@ -835,15 +845,16 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     if constexpr (PML) cp_async_wait<0>();
 }
 
-// Does the box [lo, hi] (cells, inclusive) touch a CPML slab?
-__device__ __forceinline__ bool tile_in_pml(const StepParams& p, const int lo[3], const int hi[3])
+// The CPML slab axes the box [lo, hi] (cells, inclusive) touches, bit a for
+// axis a (0: a background tile).
+__device__ __forceinline__ int tile_pml_axes(const StepParams& p, const int lo[3], const int hi[3])
 {
     const int n3[3] = {p.nx, p.ny, p.nz};
-    bool b = false;
+    int m = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-        if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) b = true;
-    return b;
+        if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) m |= 1 << a;
+    return m;
 }
 
 
@@ -860,7 +871,20 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
     const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
-    if (tile_in_pml(p, lo, hi) == PMLK) march_tma<PMLK>(p, x0, y0, k0, k1, sm);
+    const int ax = tile_pml_axes(p, lo, hi);
+    if constexpr (PMLK) {
+        // tiles touching one slab axis run code with that axis' psi only
+        if (ax == 1)
+            march_tma<true, 1>(p, x0, y0, k0, k1, sm);
+        else if (ax == 2)
+            march_tma<true, 2>(p, x0, y0, k0, k1, sm);
+        else if (ax == 4)
+            march_tma<true, 4>(p, x0, y0, k0, k1, sm);
+        else if (ax != 0)
+            march_tma<true, 7>(p, x0, y0, k0, k1, sm);
+    } else {
+        if (ax == 0) march_tma<false, 0>(p, x0, y0, k0, k1, sm);
+    }
     // the 1D incident grid and the step counter: block (0,0,0) of k_step
     if (!PMLK && bx == 0 && by == 0 && bz == 0) {
         const int tid = threadIdx.y * BX + threadIdx.x;
