@@ -54,6 +54,11 @@ class _Source(C.Structure):
                 ("t0", C.c_double), ("amp", C.c_double)]
 
 
+class _Plane(C.Structure):
+    _fields_ = [("axis", C.c_int), ("index", C.c_int), ("nf", C.c_int), ("omega", C.POINTER(C.c_double)),
+                ("K", C.c_int)]
+
+
 class _Monitors(C.Structure):
     _fields_ = [("nf", C.c_int), ("omega", C.POINTER(C.c_double)), ("abs_lo", C.c_int * 3),
                 ("abs_hi", C.c_int * 3), ("sca_lo", C.c_int * 3), ("sca_hi", C.c_int * 3),
@@ -110,6 +115,10 @@ def lib():
             L.orc_records.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
             L.orc_dft.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.orc_spectra.argtypes = [C.c_void_p] + [C.POINTER(C.c_double)] * 4
+            L.orc_set_plane.restype = C.c_int
+            L.orc_set_plane.argtypes = [C.c_void_p, C.POINTER(_Plane)]
+            L.orc_plane_dft.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double)]
+            L.orc_density.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -286,6 +295,29 @@ class Sim:
         out = [np.zeros(nf) for _ in range(4)]
         lib().orc_spectra(self._h, *[_dptr(o) for o in out])
         return dict(ext=out[0], abs=out[1], sca=out[2], inc=out[3])
+
+    def set_plane(self, axis: int, index: int, omega, K: int):
+        """Single-frequency maps on the plane normal to `axis` at node `index`
+        (E_x, E_y, E_z and div P_f, running DFT every K steps)."""
+        self._pl_omega = np.ascontiguousarray(omega, dtype=np.float64)
+        p = _Plane(axis, index, len(self._pl_omega), _dptr(self._pl_omega), K)
+        if lib().orc_set_plane(self._h, C.byref(p)) != 0:
+            raise ValueError("plane monitor rejected")
+        nz, ny, nx = self.shape3
+        self._pl_ext = (nz, ny) if axis == 0 else ((nz, nx) if axis == 1 else (ny, nx))
+
+    def plane_dft(self, which: int) -> np.ndarray:
+        """Complex [nf][n1][n2] map: which 0..2 E_x..E_z (V/m s), 3 div P_f (C/m^3 s)."""
+        n1, n2 = self._pl_ext
+        out = np.zeros((len(self._pl_omega), n1, n2, 2))
+        lib().orc_plane_dft(self._h, which, _dptr(out))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def density(self) -> np.ndarray:
+        """div P_f at every node (C/m^3), [nz][ny][nx]."""
+        out = np.zeros(self.shape3)
+        lib().orc_density(self._h, _dptr(out))
+        return out
 
 
 def run(prob: dict, steps: int | None = None, material_map=None) -> Sim:

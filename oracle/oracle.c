@@ -59,6 +59,11 @@ struct orc_sim {
     double* accH;
     int inc_node;               /* 1D node of the centre plane */
 
+    /* single-frequency plane maps */
+    orc_plane pl;
+    double* pl_omega;
+    double* pl_acc;             /* [4][nf][n1][n2][2]: E_x, E_y, E_z, div P_f */
+
     long long n;                /* time index: E^n, H^{n-1/2} are current */
 
     /* filled once at creation from the formulas below */
@@ -607,6 +612,88 @@ static void build_records(orc_sim* s)
     s->inc_node = kc - s->inc_off;
 }
 
+/* div P_f at node (i, j, k): P_a lives at the E_a site half a cell up the
+ * a axis, so the divergence at the node takes P_a(node) - P_a(node - e_a)
+ * over dx for each axis (outside the grid P_f is zero). */
+static double density_at(const orc_sim* s, int i, int j, int k)
+{
+    double d = rd(s, s->P[0], i, j, k) - rd(s, s->P[0], i - 1, j, k);
+    d += rd(s, s->P[1], i, j, k) - rd(s, s->P[1], i, j - 1, k);
+    d += rd(s, s->P[2], i, j, k) - rd(s, s->P[2], i, j, k - 1);
+    return d / s->g.dx;
+}
+
+void orc_density(const orc_sim* s, double* out)
+{
+    for (int k = 0; k < s->g.nz; ++k)
+        for (int j = 0; j < s->g.ny; ++j)
+            for (int i = 0; i < s->g.nx; ++i) out[at(s, i, j, k)] = density_at(s, i, j, k);
+}
+
+static void plane_extents(const orc_sim* s, int* n1, int* n2)
+{
+    const int n3[3] = {s->g.nx, s->g.ny, s->g.nz};
+    const int a = s->pl.axis;
+    const int slow = a == 2 ? 1 : 2, fast = a == 0 ? 1 : 0;
+    *n1 = n3[slow];
+    *n2 = n3[fast];
+}
+
+int orc_set_plane(orc_sim* s, const orc_plane* p)
+{
+    const int n3[3] = {s->g.nx, s->g.ny, s->g.nz};
+    if (p->axis < 0 || p->axis > 2 || p->index < 0 || p->index >= n3[p->axis] || p->nf < 1 || p->K < 1 || s->n != 0)
+        return -1;
+    s->pl = *p;
+    s->pl_omega = (double*)malloc(sizeof(double) * (size_t)p->nf);
+    memcpy(s->pl_omega, p->omega, sizeof(double) * (size_t)p->nf);
+    s->pl.omega = s->pl_omega;
+    int n1, n2;
+    plane_extents(s, &n1, &n2);
+    s->pl_acc = (double*)calloc((size_t)4 * p->nf * n1 * n2 * 2, sizeof(double));
+    return 0;
+}
+
+/* Plane maps (rectangle rule, reading 11): F(w) += f * exp(+i w n dt) * K dt. */
+static void plane_accumulate(orc_sim* s)
+{
+    int n1, n2;
+    plane_extents(s, &n1, &n2);
+    const int a = s->pl.axis, nf = s->pl.nf;
+    const int slow = a == 2 ? 1 : 2, fast = a == 0 ? 1 : 0;
+    const double t = s->n * s->dt, scale = s->pl.K * s->dt;
+    const size_t per = (size_t)nf * n1 * n2 * 2;
+#pragma omp parallel for schedule(static)
+    for (int u = 0; u < n1; ++u)
+        for (int v = 0; v < n2; ++v) {
+            int idx[3];
+            idx[a] = s->pl.index;
+            idx[slow] = u;
+            idx[fast] = v;
+            double val[4];
+            for (int c = 0; c < 3; ++c) val[c] = s->E[c][at(s, idx[0], idx[1], idx[2])];
+            val[3] = density_at(s, idx[0], idx[1], idx[2]);
+            for (int f = 0; f < nf; ++f) {
+                const double w = s->pl.omega[f];
+                const double cr = cos(w * t) * scale, ci = sin(w * t) * scale;
+                for (int q = 0; q < 4; ++q) {
+                    double* o = s->pl_acc + q * per + (((size_t)f * n1 + u) * n2 + v) * 2;
+                    o[0] += val[q] * cr;
+                    o[1] += val[q] * ci;
+                }
+            }
+        }
+}
+
+void orc_plane_dft(const orc_sim* s, int which, double* out)
+{
+    int n1, n2;
+    if (!s->pl_acc || which < 0 || which > 3) return;
+    plane_extents(s, &n1, &n2);
+    const size_t per = (size_t)s->pl.nf * n1 * n2 * 2;
+    memcpy(out, s->pl_acc + which * per, per * sizeof(double));
+}
+
 /* Running DFT (reading 11): called when n is a multiple of K, with E^n and
  * H^{n-1/2} current.  F(w) += f * exp(+i w t) * K dt. */
 static void dft_accumulate(orc_sim* s)
@@ -773,6 +860,8 @@ void orc_destroy(orc_sim* s)
     free(s->Einc); free(s->Hinc); free(s->psiEinc); free(s->psiHinc);
     free(s->omega); free(s->rec); free(s->coef); free(s->accE); free(s->accH);
     free(s->ctab);
+    free(s->pl_omega);
+    free(s->pl_acc);
     for (int a = 0; a < 3; ++a) { free(s->pml_b[a]); free(s->pml_c[a]); }
     free(s);
 }
@@ -802,6 +891,7 @@ static void one_step(orc_sim* s)
     }
     s->n += 1;
     if (s->nrec > 0 && s->n % s->mon.K == 0) dft_accumulate(s);
+    if (s->pl_acc && s->n % s->pl.K == 0) plane_accumulate(s);
 }
 
 void orc_step(orc_sim* s, long long nsteps)

@@ -141,6 +141,27 @@ void     orc_records(const orc_sim* s, int* rec, double* coef);
 void     orc_dft(const orc_sim* s, double* accE, double* accH);
 void     orc_spectra(const orc_sim* s, double* s_ext, double* s_abs, double* s_sca, double* inc);
 
+/* Single-frequency maps on one lattice plane (the near-field and
+ * free-electron density maps of Sec. V): plane normal to `axis` (0, 1, 2) at
+ * node index `index`; every K steps (at t = n dt, E^n and P_f^n current) the
+ * running DFT, rectangle rule as for the flux monitors, of E_x, E_y, E_z at
+ * the E-sites (i, j, k) of the plane and of the free-electron charge density
+ * div P_f (C/m^3; Eq. Nsol gives n - n0 = div P_f / e) at its nodes, by the
+ * backward differences of the Yee grid.  Set before the first step. */
+typedef struct {
+    int axis, index;
+    int nf;
+    const double* omega;     /* rad/s */
+    int K;
+} orc_plane;
+int      orc_set_plane(orc_sim* s, const orc_plane* p);
+/* which: 0..2 E_x..E_z, 3 density; out: [nf][n1][n2][2] where (n1, n2) are
+ * the plane's extents along its two other axes, slow then fast, in axis
+ * order (axis 0: [nz][ny], axis 1: [nz][nx], axis 2: [ny][nx]). */
+void     orc_plane_dft(const orc_sim* s, int which, double* out);
+/* div P_f^n at every node (C/m^3), [nz][ny][nx]. */
+void     orc_density(const orc_sim* s, double* out);
+
 #ifdef __cplusplus
 }
 #endif
