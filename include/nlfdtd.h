@@ -140,7 +140,7 @@ typedef struct {
     int abs_lo[3], abs_hi[3];
     int sca_lo[3], sca_hi[3];
     int decimate_k;           /* >= 1 */
-    int block_b;              /* samples buffered before accumulation: rounded up to 8, 16 or 32 (0 = 16) */
+    int block_b;              /* samples buffered before accumulation: rounded up to 8, 16 or 32 (0 = 32) */
 } nlf_monitors;
 
 /* Sizes and algorithmic traffic of a configured context. */
@@ -193,6 +193,26 @@ int nlf_set_source(nlf_ctx* ctx, const nlf_source* src);
 /* Monitors (copied, including omega).  Requires a source.  Errors: NLF_E_ARG,
  * NLF_E_GEOMETRY. */
 int nlf_set_monitors(nlf_ctx* ctx, const nlf_monitors* mon);
+
+/* Single-frequency maps on one lattice plane (Sec. V: the near-field
+ * amplitude and free-electron density maps; Eq. Nsol gives the density as
+ * n - n0 = div P_f / e).  Every decimate_k steps, at t = n dt, the running
+ * DFT (rectangle rule, K dt per sample, exp(+i w t)) of E_x, E_y, E_z at the
+ * E-sites (i, j, k) of the plane normal to `axis` at node `index`, and of the
+ * charge density div P_f (C/m^3) at its nodes, by the backward differences
+ * of the Yee grid.  nf <= NLF_PLANE_MAX_NF; with flux monitors set,
+ * decimate_k must equal theirs.  Set before the first run; a context with a
+ * plane monitor is not accepted by nlf_batch_run.  Copied.  Errors: NLF_E_ARG,
+ * NLF_E_STATE. */
+#define NLF_PLANE_MAX_NF 16
+typedef struct {
+    int axis;                 /* 0, 1, 2: the plane's normal */
+    int index;                /* node index along axis */
+    int nf;
+    const double* omega;      /* rad/s */
+    int decimate_k;
+} nlf_plane_monitor;
+int nlf_set_plane_monitor(nlf_ctx* ctx, const nlf_plane_monitor* mon);
 
 /* Bytes of device state the context needs (for admission by HBM budget).
  * Valid after materials, shapes/map, source and monitors are set; 0 on error. */
@@ -248,6 +268,15 @@ int nlf_get_spectra(nlf_ctx* ctx, double* s_ext, double* s_abs, double* s_sca);
  * low face then high face, term (+E_b H_c, then -E_c H_b with (a,b,c)
  * cyclic), slower in-plane axis outer; the last record is the incident field. */
 int nlf_get_dft(nlf_ctx* ctx, double* dst);
+
+/* One plane map (nlf_set_plane_monitor): which = NLF_FIELD_EX .. EZ or
+ * NLF_MAP_DENSITY; host dst of nf * n1 * n2 * 2 doubles [f][n1][n2][re, im],
+ * (n1, n2) the plane's extents along its other two axes, slower first
+ * (axis 0: nz, ny; axis 1: nz, nx; axis 2: ny, nx).  E in V/m s, density
+ * in C/m^3 s.  Errors: NLF_E_ARG, NLF_E_STATE (no plane monitor or no run),
+ * NLF_E_CUDA. */
+#define NLF_MAP_DENSITY 9
+int nlf_get_plane_map(nlf_ctx* ctx, int which, double* dst);
 long long nlf_num_records(const nlf_ctx* ctx);
 
 /* Checkpoint: copy the whole device state (nlf_state_bytes bytes, including

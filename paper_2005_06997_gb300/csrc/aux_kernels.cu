@@ -144,25 +144,13 @@ __global__ void k_dft_phase(const DftParams d, int count)
     d.phase[t] = v;
 }
 
-// One flush of the running DFT: block = up to 256 frequencies of one
-// frequency chunk x RCH records (accum_records).
+// One flush of the running DFT: block = ACC_NT frequencies x ACC_NCH chunks
+// of RCH records (accum_block).
 template <int B, int RCH>
-__global__ void __launch_bounds__(256) k_dft_accum(const DftParams d)
+__global__ void __launch_bounds__(ACC_NT) k_dft_accum(const DftParams d)
 {
-    __shared__ float sE[B][RCH];
-    __shared__ float sH[B][RCH];
-    const long long r0 = (long long)blockIdx.x * RCH;
-    const int f = blockIdx.y * blockDim.x + threadIdx.x;
-    const long long nr = d.nrec + 1;
-    for (int t = threadIdx.x; t < B * RCH; t += blockDim.x) {
-        const int s = t / RCH, rr = t - s * RCH;
-        const long long r = r0 + rr;
-        sE[s][rr] = r < nr ? d.sE[(long long)s * nr + r] : 0.f;
-        sH[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
-    }
-    __syncthreads();
-    if (f >= d.nf) return;
-    accum_records<B, RCH>(d, r0, f, sE, sH);
+    __shared__ AccShared<B, RCH> sm;
+    accum_block<B, RCH>(d, (long long)blockIdx.x * RCH * ACC_NCH, ACC_NCH, blockIdx.y * ACC_NT, sm);
 }
 
 void launch_dft_gather(const DftParams& d, const float* E, const float* H, const float* e_inc, const float* h_inc,
@@ -177,16 +165,14 @@ void launch_dft_flush(const DftParams& d, int count, cudaStream_t st)
     const int np = d.B * d.nf;
     k_dft_phase<<<(np + 255) / 256, 256, 0, st>>>(d, count);
     constexpr int RCH = 32;
-    // one frequency chunk of up to 256 threads (whole warps) per block row
-    const int chunks = (d.nf + 255) / 256;
-    const int nt = ((d.nf + chunks - 1) / chunks + 31) / 32 * 32;
-    dim3 grd((unsigned)((d.nrec + 1 + RCH - 1) / RCH), (unsigned)((d.nf + nt - 1) / nt));
+    constexpr long long per = (long long)RCH * ACC_NCH;
+    dim3 grd((unsigned)((d.nrec + 1 + per - 1) / per), (unsigned)((d.nf + ACC_NT - 1) / ACC_NT));
     if (d.B <= 8)
-        k_dft_accum<8, RCH><<<grd, nt, 0, st>>>(d);
+        k_dft_accum<8, RCH><<<grd, ACC_NT, 0, st>>>(d);
     else if (d.B <= 16)
-        k_dft_accum<16, RCH><<<grd, nt, 0, st>>>(d);
+        k_dft_accum<16, RCH><<<grd, ACC_NT, 0, st>>>(d);
     else
-        k_dft_accum<32, RCH><<<grd, nt, 0, st>>>(d);
+        k_dft_accum<32, RCH><<<grd, ACC_NT, 0, st>>>(d);
 }
 
 // ----------------------------------------------------------------- fluxes
@@ -244,6 +230,74 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
 }  // namespace nlf
 
 namespace nlf {
+
+// P_f component c (P/eps0) at node (i, j, k); zero outside the metal box.
+__device__ __forceinline__ float plane_p(const PlaneParams& m, const float* const* P, int c, int i, int j, int k)
+{
+    const int bi = i - m.bb_lo[0], bj = j - m.bb_lo[1], bk = k - m.bb_lo[2];
+    if (!m.has_metal || bi < 0 || bj < 0 || bk < 0 || bi >= m.bb_n[0] || bj >= m.bb_n[1] || bk >= m.bb_n[2])
+        return 0.f;
+    return __ldg(P[c] + ((size_t)bk * m.bb_n[1] + bj) * m.bb_n[0] + bi);
+}
+
+// One sample of the plane maps at time index n (read from the device step
+// counter, so that a replayed graph samples the right time): E^n at the
+// plane's E-sites and div P_f^n (backward differences, C/m^3) at its nodes,
+// added with exp(+i w n dt) K dt.  The block stages the nf phases (FP64).
+__global__ void __launch_bounds__(256) k_plane_dft(const PlaneParams m, const float* E0, const float* E1,
+                                                   const float* E2, const float* P0, const float* P1, const float* P2,
+                                                   const long long* step)
+{
+    __shared__ double2 ph[NLF_PLANE_MAX_NF_DEV];
+    if (threadIdx.x < m.nf) {
+        double s, c;
+        sincos(m.omega[threadIdx.x] * (double)(*step) * m.dt, &s, &c);
+        ph[threadIdx.x] = make_double2(c * m.scale, s * m.scale);
+    }
+    __syncthreads();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long np = (long long)m.n1 * m.n2;
+    if (t >= np) return;
+    const int u = (int)(t / m.n2), v = (int)(t - (long long)u * m.n2);
+    int idx[3];
+    const int slow = m.axis == 2 ? 1 : 2, fast = m.axis == 0 ? 1 : 0;
+    idx[m.axis] = m.index;
+    idx[slow] = u;
+    idx[fast] = v;
+    const int i = idx[0], j = idx[1], k = idx[2];
+    const size_t q = ((size_t)k * m.ny + j) * m.px + i;
+    const float* P[3] = {P0, P1, P2};
+    float val[4];
+    val[0] = __ldg(E0 + q);
+    val[1] = __ldg(E1 + q);
+    val[2] = __ldg(E2 + q);
+    val[3] = 0.f;
+    if (m.has_metal) {
+        const float d = (plane_p(m, P, 0, i, j, k) - plane_p(m, P, 0, i - 1, j, k)) +
+                        (plane_p(m, P, 1, i, j, k) - plane_p(m, P, 1, i, j - 1, k)) +
+                        (plane_p(m, P, 2, i, j, k) - plane_p(m, P, 2, i, j, k - 1));
+        val[3] = (float)(d * m.eps0_dx);
+    }
+    for (int f = 0; f < m.nf; ++f) {
+        const double2 p = ph[f];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            double2* a = m.acc + ((size_t)w * m.nf + f) * np + t;
+            double2 x = *a;
+            x.x += (double)val[w] * p.x;
+            x.y += (double)val[w] * p.y;
+            *a = x;
+        }
+    }
+}
+
+void launch_plane_dft(const PlaneParams& m, const float* const* E, const float* const* P, const long long* step,
+                      cudaStream_t st)
+{
+    const long long np = (long long)m.n1 * m.n2;
+    k_plane_dft<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(m, E[0], E[1], E[2], P ? P[0] : nullptr,
+                                                              P ? P[1] : nullptr, P ? P[2] : nullptr, step);
+}
 
 // Copy one field component out of the padded layout (rows of px floats, nx
 // used) into a dense [nz][ny][nx] array, scaled.

@@ -81,25 +81,15 @@ __global__ void k_phase_batch(const BatchDft a, int count)
 // Same arithmetic as the single-grid accumulation: per record chunk and
 // frequency chunk, FP32 sums over the B samples added into FP64.
 template <int B, int RCH>
-__global__ void __launch_bounds__(128) k_accum_batch(const BatchDft a)
+__global__ void __launch_bounds__(ACC_NT) k_accum_batch(const BatchDft a)
 {
-    __shared__ float sEs[B][RCH];
-    __shared__ float sHs[B][RCH];
+    __shared__ AccShared<B, RCH> sm;
     const long long w = blockIdx.x;
     const int q = find_inst(a.chunk_end, a.n, w);
     const DftParams& d = a.inst[q].d;
-    const long long r0 = (w - (q > 0 ? a.chunk_end[q - 1] : 0)) * RCH;
-    const int f = blockIdx.y * blockDim.x + threadIdx.x;
-    const long long nr = d.nrec + 1;
-    for (int t = threadIdx.x; t < B * RCH; t += blockDim.x) {
-        const int s = t / RCH, rr = t - s * RCH;
-        const long long r = r0 + rr;
-        sEs[s][rr] = r < nr ? d.sE[(long long)s * nr + r] : 0.f;
-        sHs[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
-    }
-    __syncthreads();
-    if (f >= d.nf) return;
-    accum_records<B, RCH>(d, r0, f, sEs, sHs);
+    const int f0 = blockIdx.y * ACC_NT;
+    if (f0 >= d.nf) return;
+    accum_block<B, RCH>(d, (w - (q > 0 ? a.chunk_end[q - 1] : 0)) * RCH, 1, f0, sm);
 }
 
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st)
@@ -111,13 +101,13 @@ void launch_flush_batch(const BatchDft& a, long long total_phase, long long tota
                         int count, cudaStream_t st)
 {
     k_phase_batch<<<(unsigned)((total_phase + 255) / 256), 256, 0, st>>>(a, count);
-    dim3 grd((unsigned)total_chunks, (max_nf + 127) / 128);
+    dim3 grd((unsigned)total_chunks, (max_nf + ACC_NT - 1) / ACC_NT);
     if (B <= 8)
-        k_accum_batch<8, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+        k_accum_batch<8, NLF_BATCH_RCH><<<grd, ACC_NT, 0, st>>>(a);
     else if (B <= 16)
-        k_accum_batch<16, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+        k_accum_batch<16, NLF_BATCH_RCH><<<grd, ACC_NT, 0, st>>>(a);
     else
-        k_accum_batch<32, NLF_BATCH_RCH><<<grd, 128, 0, st>>>(a);
+        k_accum_batch<32, NLF_BATCH_RCH><<<grd, ACC_NT, 0, st>>>(a);
 }
 
 }  // namespace nlf

@@ -41,6 +41,8 @@ void launch_dft_gather(const DftParams& d, const float* E, const float* H, const
 void launch_dft_flush(const DftParams& d, int count, cudaStream_t st);
 void launch_flux(const double2* accE, const double2* accH, const double* coef, long long n_abs, long long nrec,
                  int nf, double2* partial, int G, double dA, double* out, cudaStream_t st);
+void launch_plane_dft(const PlaneParams& m, const float* const* E, const float* const* P, const long long* step,
+                      cudaStream_t st);
 void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st);
@@ -82,6 +84,11 @@ struct nlf_ctx {
     bool have_src = false;
     nlf_source src{};
     bool have_mon = false;
+    bool have_plane = false;
+    nlf_plane_monitor plane{};
+    std::vector<double> plane_omega;
+    size_t off_pacc = 0, off_pomega = 0;
+    nlf::PlaneParams pp{};
     nlf_monitors mon{};
     std::vector<double> omega;
     std::string err;
@@ -371,7 +378,7 @@ int plan(nlf_ctx* c)
     if (c->have_mon) {
         c->K = c->mon.decimate_k;
         // the accumulation kernel is instantiated for 8, 16 and 32 buffered samples
-        const int bb = c->mon.block_b > 0 ? c->mon.block_b : 16;
+        const int bb = c->mon.block_b > 0 ? c->mon.block_b : 32;
         c->B = bb <= 8 ? 8 : (bb <= 16 ? 16 : 32);
         std::vector<uint32_t> re, rh, rs;
         std::vector<double> co;
@@ -385,6 +392,11 @@ int plan(nlf_ctx* c)
         c->U = (int)(kb % 2 == 0 ? kb : 2 * kb);
     } else {
         c->U = 128;
+    }
+    // a captured period must hold a whole number of plane samples
+    if (c->have_plane && !c->have_mon) {
+        const long long kp = 16LL * c->plane.decimate_k;
+        c->U = (int)(kp % 2 == 0 ? kp : 2 * kp);
     }
     // layout
     size_t o = 0;
@@ -436,6 +448,14 @@ int plan(nlf_ctx* c)
         c->off_acc = take(2 * nr1 * nf * sizeof(double2));
         c->off_partial = take((size_t)c->G * nf * sizeof(double2));
         c->off_out = take(4 * nf * sizeof(double));
+    }
+    if (c->have_plane) {
+        const long long n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+        const int a = c->plane.axis, slow = a == 2 ? 1 : 2, fast = a == 0 ? 1 : 0;
+        c->pp.n1 = (int)n3[slow];
+        c->pp.n2 = (int)n3[fast];
+        c->off_pomega = take((size_t)c->plane.nf * sizeof(double));
+        c->off_pacc = take((size_t)4 * c->plane.nf * c->pp.n1 * c->pp.n2 * sizeof(double2));
     }
     c->bytes = o;
     c->planned = true;
@@ -568,6 +588,26 @@ void fill_params(nlf_ctx* c)
         p.step0 = &h->step[r];
         p.step1 = &h->step[w];
         p.err = &h->err;
+    }
+    if (c->have_plane) {
+        nlf::PlaneParams& m = c->pp;
+        m.axis = c->plane.axis;
+        m.index = c->plane.index;
+        m.nx = c->g.nx;
+        m.ny = c->g.ny;
+        m.nz = c->g.nz;
+        m.px = c->px;
+        m.nf = c->plane.nf;
+        m.omega = at<double>(c, c->off_pomega);
+        m.dt = c->dt;
+        m.scale = c->plane.decimate_k * c->dt;
+        m.eps0_dx = kEps0 / c->g.dx;
+        m.has_metal = c->has_metal;
+        for (int a2 = 0; a2 < 3; ++a2) {
+            m.bb_lo[a2] = c->bb_lo[a2];
+            m.bb_n[a2] = c->bb_n[a2];
+        }
+        m.acc = at<double2>(c, c->off_pacc);
     }
     if (c->have_mon) {
         nlf::DftParams& d = c->dp;
@@ -702,6 +742,9 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         if ((rc = put(c->off_dcoef, co.data(), co.size() * sizeof(double)))) return rc;
         if ((rc = put(c->off_omega, c->omega.data(), c->omega.size() * sizeof(double)))) return rc;
     }
+    if (c->have_plane &&
+        (rc = put(c->off_pomega, c->plane_omega.data(), c->plane_omega.size() * sizeof(double))))
+        return rc;
     if (c->has_metal) {
         nlf::SiteGeom sg{};
         for (int a = 0; a < 3; ++a) {
@@ -805,6 +848,17 @@ void step_once(nlf_ctx* c, cudaStream_t st)
 // The running-DFT work due after time step n (c->n already advanced).
 void monitor_work(nlf_ctx* c, cudaStream_t st)
 {
+    if (c->have_plane && c->n % c->plane.decimate_k == 0) {
+        const int cur = (int)(c->n & 1);
+        const float* E[3];
+        const float* P[3];
+        for (int q = 0; q < 3; ++q) {
+            E[q] = at<float>(c, c->off_E[cur]) + (size_t)q * c->nfield;
+            P[q] = c->has_metal ? at<float>(c, c->off_P[cur]) + (size_t)q * c->nbb : nullptr;
+        }
+        nlf::launch_plane_dft(c->pp, E, c->has_metal ? P : nullptr, &at<Header>(c, c->off_hdr)->step[cur], st);
+        c->launches += 1;
+    }
     if (c->have_mon && c->n % c->K == 0) {
         const int cur = (int)(c->n & 1);
         Header* h = at<Header>(c, c->off_hdr);
@@ -1261,11 +1315,45 @@ int nlf_set_monitors(nlf_ctx* c, const nlf_monitors* m)
         return NLF_E_ARG;
     if (c->ready) return fail(c, NLF_E_STATE, "monitors are fixed after the first run");
     if (!c->have_src) return fail(c, NLF_E_STATE, "set the source before the monitors");
+    if (c->have_plane && m->decimate_k != c->plane.decimate_k)
+        return fail(c, NLF_E_ARG, "monitor decimate_k must equal the plane monitor's");
     c->mon = *m;
     c->omega.assign(m->omega, m->omega + m->nf);
     c->mon.omega = c->omega.data();
     c->have_mon = true;
     c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_set_plane_monitor(nlf_ctx* c, const nlf_plane_monitor* m)
+{
+    if (!c || !m || m->axis < 0 || m->axis > 2 || m->nf < 1 || m->nf > NLF_PLANE_MAX_NF || !m->omega ||
+        m->decimate_k < 1)
+        return NLF_E_ARG;
+    const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+    if (m->index < 0 || m->index >= n3[m->axis]) return fail(c, NLF_E_ARG, "plane index outside the grid");
+    if (c->ready) return fail(c, NLF_E_STATE, "the plane monitor is fixed after the first run");
+    if (c->have_mon && m->decimate_k != c->mon.decimate_k)
+        return fail(c, NLF_E_ARG, "plane decimate_k must equal the flux monitors'");
+    c->plane = *m;
+    c->plane_omega.assign(m->omega, m->omega + m->nf);
+    c->plane.omega = c->plane_omega.data();
+    c->have_plane = true;
+    c->planned = false;
+    return NLF_OK;
+}
+
+int nlf_get_plane_map(nlf_ctx* c, int which, double* dst)
+{
+    if (!c || !dst || !((which >= NLF_FIELD_EX && which <= NLF_FIELD_EZ) || which == NLF_MAP_DENSITY))
+        return NLF_E_ARG;
+    if (!c->have_plane || !c->ready) return fail(c, NLF_E_STATE, "no plane monitor or no run yet");
+    CK(cudaStreamSynchronize(c->stream));
+    const int w = which == NLF_MAP_DENSITY ? 3 : which;
+    const size_t per = (size_t)c->plane.nf * c->pp.n1 * c->pp.n2;
+    CK(cudaMemcpy(dst, c->base + c->off_pacc + (size_t)w * per * sizeof(double2), per * sizeof(double2),
+                  cudaMemcpyDeviceToHost));
+    c->d2h += (long long)(per * sizeof(double2));
     return NLF_OK;
 }
 
@@ -1574,7 +1662,7 @@ int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* stream, i
     std::vector<int> batchable;
     for (int q = 0; q < n; ++q) {
         nlf_ctx* c = ctxs[q];
-        if (!c || steps[q] < 0) {
+        if (!c || steps[q] < 0 || c->have_plane) {   // plane maps are single-grid only
             rc[q] = NLF_E_ARG;
             continue;
         }

@@ -126,6 +126,22 @@ struct VoxParams {
     const int* free_e;            // [NLF_MAX_MAT + 1] material has free electrons
 };
 
+// Single-frequency plane maps: running DFT of E_x, E_y, E_z and of div P_f on
+// one lattice plane.
+#define NLF_PLANE_MAX_NF_DEV 16
+struct PlaneParams {
+    int axis, index;
+    int nx, ny, nz, px;
+    int n1, n2;                 // plane extents along its other axes, slow then fast
+    int nf;
+    const double* omega;        // [nf] rad/s
+    double dt, scale;           // scale = K dt (rectangle rule)
+    double eps0_dx;             // eps0 / dx: P/eps0 difference units -> C/m^3
+    int has_metal;
+    int bb_lo[3], bb_n[3];
+    double2* acc;               // [4][nf][n1][n2]
+};
+
 // Where the metal box sits in the field arrays (for the site list).
 struct SiteGeom {
     int bb_lo[3], bb_n[3];

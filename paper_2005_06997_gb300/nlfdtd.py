@@ -50,6 +50,14 @@ class nlf_source(C.Structure):
                 ("amplitude", C.c_double)]
 
 
+class nlf_plane_monitor(C.Structure):
+    _fields_ = [("axis", C.c_int), ("index", C.c_int), ("nf", C.c_int), ("omega", C.POINTER(C.c_double)),
+                ("decimate_k", C.c_int)]
+
+
+NLF_MAP_DENSITY = 9
+
+
 class nlf_monitors(C.Structure):
     _fields_ = [("nf", C.c_int), ("omega", C.POINTER(C.c_double)), ("abs_lo", C.c_int * 3),
                 ("abs_hi", C.c_int * 3), ("sca_lo", C.c_int * 3), ("sca_hi", C.c_int * 3),
@@ -73,6 +81,8 @@ SIGNATURES = {
     "nlf_set_material_map": (C.c_int, [_P, C.c_void_p, C.c_int]),
     "nlf_set_source": (C.c_int, [_P, C.POINTER(nlf_source)]),
     "nlf_set_monitors": (C.c_int, [_P, C.POINTER(nlf_monitors)]),
+    "nlf_set_plane_monitor": (C.c_int, [_P, C.POINTER(nlf_plane_monitor)]),
+    "nlf_get_plane_map": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
     "nlf_state_bytes": (C.c_size_t, [_P]),
     "nlf_bind_state": (C.c_int, [_P, C.c_void_p, C.c_size_t]),
     "nlf_run": (C.c_int, [_P, C.c_longlong, C.c_void_p]),
@@ -199,7 +209,7 @@ def make_source(s) -> nlf_source:
     return o
 
 
-def make_monitors(m, block_b=16):
+def make_monitors(m, block_b=32):
     omega = np.ascontiguousarray(m["omega"], dtype=np.float64)
     o = nlf_monitors()
     o.nf = len(omega)
@@ -217,7 +227,7 @@ def make_monitors(m, block_b=16):
 class Solver:
     """One configured context (nlf_create + nlf_set_*) for a problem dict."""
 
-    def __init__(self, prob: dict, material_map=None, block_b: int = 16):
+    def __init__(self, prob: dict, material_map=None, block_b: int = 32):
         require_gpu()
         L = load()
         self.L = L
@@ -244,6 +254,16 @@ class Solver:
             _check(h, L.nlf_set_monitors(h, C.byref(mon)))
         self.shape3 = tuple(reversed(prob["shape"]))
         self.nf = len(prob["monitors"]["omega"]) if prob.get("monitors") is not None else 0
+        pm = prob.get("plane_map")
+        if pm is not None:
+            # {"axis", "index", "omega", "K"}: single-frequency maps on one plane
+            self._pl_omega = np.ascontiguousarray(pm["omega"], dtype=np.float64)
+            m = nlf_plane_monitor(int(pm["axis"]), int(pm["index"]), len(self._pl_omega),
+                                  self._pl_omega.ctypes.data_as(C.POINTER(C.c_double)), int(pm["K"]))
+            _check(h, L.nlf_set_plane_monitor(h, C.byref(m)))
+            nz, ny, nx = self.shape3
+            a = int(pm["axis"])
+            self._pl_ext = (nz, ny) if a == 0 else ((nz, nx) if a == 1 else (ny, nx))
 
     def close(self):
         if getattr(self, "h", None):
@@ -255,6 +275,14 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def plane_map(self, which) -> np.ndarray:
+        """Complex [nf][n1][n2] plane map: "Ex", "Ey", "Ez" or "density"."""
+        code = {"Ex": 0, "Ey": 1, "Ez": 2, "density": NLF_MAP_DENSITY}[which]
+        n1, n2 = self._pl_ext
+        out = np.zeros((len(self._pl_omega), n1, n2, 2))
+        _check(self.h, self.L.nlf_get_plane_map(self.h, code, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out[..., 0] + 1j * out[..., 1]
 
     def state_bytes(self) -> int:
         return int(self.L.nlf_state_bytes(self.h))
