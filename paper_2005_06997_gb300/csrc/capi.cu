@@ -128,7 +128,7 @@ struct nlf_ctx {
     cudaEvent_t done = nullptr;
     cudaStream_t cap = nullptr;         // private stream for graph capture
     cudaStream_t aux = nullptr;         // second stream of the step: the CPML tiles
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     long long n = 0;                    // time index
@@ -804,6 +804,8 @@ int ensure_ready(nlf_ctx* c, cudaStream_t st)
     if (!c->aux) CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     if (!c->join) CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+    if (!c->fork2) CK(cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming));
+    if (!c->join2) CK(cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming));
     return initialise(c, st);
 }
 
@@ -827,8 +829,29 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
         nlf::launch_step(sp, st);
         c->launches += 1;
     }
-    if (nlf::tfsf_items(sp) > 0) {
+}
+
+// The work after the EM step of time step n: the TF/SF corrections and the
+// material update touch disjoint cells (material sites lie two cells inside
+// the TF surface), so with both present the corrections run on the second
+// stream beside the material update.
+void launch_post(nlf_ctx* c, cudaStream_t st)
+{
+    const nlf::StepParams& sp = c->sp[c->n & 1];
+    const bool tf = nlf::tfsf_items(sp) > 0, met = c->n_msites > 0;
+    if (tf && met) {
+        cudaEventRecord(c->fork2, st);
+        cudaStreamWaitEvent(c->aux, c->fork2, 0);
+        nlf::launch_tfsf(sp, c->aux);
+        nlf::launch_metal(sp, c->n_msites, st);
+        cudaEventRecord(c->join2, c->aux);
+        cudaStreamWaitEvent(st, c->join2, 0);
+        c->launches += 2;
+    } else if (tf) {
         nlf::launch_tfsf(sp, st);
+        c->launches += 1;
+    } else if (met) {
+        nlf::launch_metal(sp, c->n_msites, st);
         c->launches += 1;
     }
 }
@@ -837,10 +860,7 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
 void step_once(nlf_ctx* c, cudaStream_t st)
 {
     launch_em(c, st);
-    if (c->n_msites > 0) {
-        nlf::launch_metal(c->sp[c->n & 1], c->n_msites, st);
-        c->launches += 1;
-    }
+    launch_post(c, st);
     c->n += 1;
     monitor_work(c, st);
 }
@@ -1443,10 +1463,7 @@ int nlf_time_kernels(nlf_ctx* c, long long steps, void* stream, double* ms_out)
         cudaEventRecordWithFlags(e[0], c->cap, cudaEventRecordExternal);
         launch_em(c, c->cap);
         cudaEventRecordWithFlags(e[1], c->cap, cudaEventRecordExternal);
-        if (c->n_msites > 0) {
-            nlf::launch_metal(c->sp[c->n & 1], c->n_msites, c->cap);
-            c->launches += 1;
-        }
+        launch_post(c, c->cap);
         cudaEventRecordWithFlags(e[2], c->cap, cudaEventRecordExternal);
         c->n += 1;
         monitor_work(c, c->cap);
@@ -1749,6 +1766,8 @@ void nlf_destroy(nlf_ctx* c)
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
+    if (c->fork2) cudaEventDestroy(c->fork2);
+    if (c->join2) cudaEventDestroy(c->join2);
     if (c->owned && c->base) cudaFree(c->base);
     delete c;
 }

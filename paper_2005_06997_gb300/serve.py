@@ -57,7 +57,7 @@ class Server:
         self.launches = 0
 
     def _admit(self, req, now):
-        s = nlfdtd.Solver(req)
+        s = nlfdtd.Solver(req, block_b=SERVE_B)
         nb = s.state_bytes()
         buf = self.torch.empty(nb + 256, dtype=self.torch.uint8, device="cuda")
         ptr = (buf.data_ptr() + 255) // 256 * 256
@@ -72,7 +72,7 @@ class Server:
             req = waiting[0]
             key = id(req)
             if key not in sizes:
-                probe = nlfdtd.Solver(req)
+                probe = nlfdtd.Solver(req, block_b=SERVE_B)
                 sizes[key] = probe.state_bytes()
                 probe.close()
             if self.used + sizes[key] > self.budget and active:
@@ -135,12 +135,17 @@ class Server:
         return results, summarise(results, wall)
 
 
+# Samples buffered per DFT flush for served requests: a batched segment is one
+# DFT period (K * SERVE_B steps), so this sets how often finished requests
+# leave and new ones join.
+SERVE_B = 16
+
+
 def _period(a):
     """Time steps of one DFT period of an active request (the batching unit)."""
     mon = a.req.get("monitors")
     K = mon.get("K", 16) if mon else 1
-    B = 16
-    kb = K * B
+    kb = K * SERVE_B
     return kb if kb % 2 == 0 else 2 * kb
 
 
