@@ -145,6 +145,35 @@ def oracle_sample(prob, steps, gpu_check=False):
     return cells * steps / dt / 1e9, dt, acc
 
 
+def oracle_one_thread(steps):
+    """The oracle on `steps` steps of the workload with one host thread (a
+    separate process, since the OpenMP team size is fixed at first use)."""
+    code = ("import sys, time, math; sys.path.insert(0, %r); import oracle; "
+            "from paper_2005_06997_gb300 import workloads as W; p = W.CONFIGS[%r](); s = oracle.Sim(p); "
+            "t = time.perf_counter(); s.step(%d); dt = time.perf_counter() - t; "
+            "print(math.prod(p['shape']) * %d / dt / 1e9, dt)") % (ROOT, WORKLOAD, steps, steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    v, dt = out.stdout.split()[-2:]
+    return float(v), float(dt)
+
+
+def replica_time_ms(local_ms, dist, device):
+    """Replicas only: every rank solves its own grid; the job time is the
+    slowest rank's (all ranks receive it)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, cell_updates_per_rank, job_ms):
+    """Whole-job Gcell-updates/s: the cell updates of all ranks over the job time."""
+    return world * cell_updates_per_rank / (job_ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     from paper_2005_06997_gb300 import workloads as W
     prob = W.CONFIGS[WORKLOAD]()
@@ -232,11 +261,7 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     clk = clocks.stop()
     launches = solver.launches - launches0
-    total_ms = t_start.elapsed_time(t_stop)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replica_time_ms(t_start.elapsed_time(t_stop), dist, "cuda")
     n_timed = tail * len(kernel_ev)
     k_mean_ms = sum(t["step_ms"] for t in kernel_ev) / n_timed
     m_mean_ms = sum(t["metal_ms"] for t in kernel_ev) / n_timed
@@ -245,7 +270,7 @@ def run_ours(args, rank, world, dist):
     step_kernel_bytes = info["step_kernel_bytes"]
     metal_kernel_bytes = info["metal_kernel_bytes"]
     achieved = step_kernel_bytes / (k_mean_ms * 1e-3) / 1e9
-    value = world * args.steps * steps * cells / (total_ms * 1e-3) / 1e9
+    value = replica_value(world, args.steps * steps * cells, total_ms)
 
     # end to end through the public API: create, upload, solve, read the spectra
     torch.cuda.synchronize()
@@ -276,6 +301,11 @@ def run_ours(args, rank, world, dist):
                "kind": "oracle", "sample": "%d time steps of the %s grid (FP64 oracle, %.1f s)" %
                (sample, WORKLOAD, dt),
                "gpu_rel_l2_vs_oracle": acc}
+        try:
+            v1, dt1 = oracle_one_thread(2)
+            cpu["one_thread"] = {"value": v1, "sample": "2 time steps, one host thread (%.1f s)" % dt1}
+        except Exception as e:              # report, do not fail the benchmark line
+            cpu["one_thread"] = {"error": str(e)[:200]}
 
     if rank == 0:
         traffic = None
