@@ -1049,6 +1049,11 @@ __device__ __forceinline__ void tfsf_item(const StepParams& p, long long t)
         k = l2 + (int)(r >> 1);
         v = dz(j, k);
     }
+    // a TF surface one cell from a wall: tangential E on index 0 is the wall
+    // (held at zero) and index n lies beyond it, so neither is corrected
+    if (!isH && ((comp != 0 && i == 0) || (comp != 1 && j == 0) || (comp != 2 && k == 0) || i >= p.nx ||
+                 j >= p.ny || k >= p.nz))
+        return;
     const uint32_t q = ((uint32_t)k * p.ny + j) * p.px + i;
     float* f = isH ? p.H1[comp] : p.E1[comp];
     f[q] += v;

@@ -127,6 +127,29 @@ def test_fields_ragged_grid_local_drude():
     assert_fields_match(g, o)
 
 
+@pytest.mark.parametrize("tf_box", [((2, 1, 3), (11, 9, 15)), ((1, 1, 1), (12, 10, 17))],
+                         ids=["inner", "at_the_walls"])
+def test_fields_grid_narrower_than_one_tile(tf_box):
+    """A 13 x 11 x 18 PEC box: one partial tile along x (tiles are 32 x 8
+    cells), a full and a 3-row tile along y, a TF/SF source and a small GNOR
+    sphere (three cells across, three cells from the walls); no flux
+    monitors.  The TF surface lies one cell from a wall: its corrections must
+    leave the tangential E of the wall at zero and write nothing beyond the
+    grid."""
+    prob = W.small_sphere(n=36, steps=0, nf=4, K=4)
+    prob["shape"] = (13, 11, 18)
+    prob["pml"] = 0
+    prob["bc"] = ("pec",) * 3
+    prob["monitors"] = None
+    prob["shapes"] = [W.sphere_shape((13, 8, 18), 2, 1)]
+    src = prob["source"]
+    src["tf_lo"], src["tf_hi"] = tf_box
+    prob = early_pulse(prob)
+    g, o = run_pair(prob, 400)
+    assert np.max(np.abs(o.array("Px"))) > 0
+    assert_fields_match(g, o)
+
+
 def test_fields_pole_only_dielectric_and_pec_walls():
     """No free electrons (wp = 0) with two critical points (phi != 0), PEC
     walls on one axis: exercises f3 alone and the wall handling."""
