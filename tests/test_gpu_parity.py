@@ -150,6 +150,24 @@ def test_fields_grid_narrower_than_one_tile(tf_box):
     assert_fields_match(g, o)
 
 
+@pytest.mark.parametrize("bc", [("pec", "cpml", "pec"), ("cpml", "pec", "pec")], ids=["cpml_y", "cpml_x"])
+def test_fields_cpml_on_one_axis_and_a_one_plane_chunk(bc):
+    """A 40 x 44 x 17 grid with a 6-cell CPML on one axis and PEC walls on
+    the others (CPML tiles of one slab axis beside PEC walls), z chunks of
+    8, 8 and 1 planes, a TF/SF source and a GNOR sphere."""
+    n3, L = (40, 44, 17), 6
+    prob = W.small_sphere(n=36, steps=0, nf=4, K=4)
+    prob["shape"], prob["pml"], prob["bc"], prob["monitors"] = n3, L, bc, None
+    prob["shapes"] = [W.sphere_shape(n3, 6, 1)]
+    lo = tuple(L + 1 if b == "cpml" else 2 for b in bc)
+    hi = tuple(n - L - 2 if b == "cpml" else n - 3 for n, b in zip(n3, bc))
+    prob["source"]["tf_lo"], prob["source"]["tf_hi"] = lo, hi
+    prob = early_pulse(prob)
+    g, o = run_pair(prob, 400)
+    assert np.max(np.abs(o.array("Px"))) > 0
+    assert_fields_match(g, o)
+
+
 def test_fields_pole_only_dielectric_and_pec_walls():
     """No free electrons (wp = 0) with two critical points (phi != 0), PEC
     walls on one axis: exercises f3 alone and the wall handling."""
