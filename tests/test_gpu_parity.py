@@ -223,6 +223,27 @@ def test_dft_and_spectra_parity():
     assert abs(w[np.argmax(sg["ext"])] / w[np.argmax(so["ext"])] - 1) <= 1e-3
 
 
+def test_dielectric_background_and_another_courant_number():
+    """The GNOR + pole sphere in a background of eps_b = 1.77 at S = 0.45:
+    fields, FP64 accumulators and cross sections against the oracle (the
+    background enters the update, the 1D incident grid, the CPML grading and
+    the flux normalisation)."""
+    prob = W.small_sphere(n=36, steps=0, nf=16, K=4, band_ev=(1.5, 8.5))
+    prob["eps_b"], prob["courant"] = 1.77, 0.45
+    prob = early_pulse(prob, band=(1.5, 8.5))
+    g, o = run_pair(prob, 2000, block_b=16)
+    assert_fields_match(g, o)
+    aEg, aHg = g.dft()
+    aEo, aHo = o.dft()
+    assert rel_l2(aEg, aEo) < 1e-4
+    assert rel_l2(aHg, aHo) < 1e-4
+    sg, so = g.spectra(), o.spectra()
+    sel = so["inc"] >= 1e-3 * so["inc"].max()
+    for key in ("ext", "abs", "sca"):
+        err = np.abs(sg[key][sel] - so[key][sel]) / np.max(np.abs(so[key][sel]))
+        assert np.max(err) <= TOL_SIGMA, (key, np.max(err))
+
+
 def test_sphere_ag_48_configuration():
     """The 48^3 Ag-like sphere configuration, 1000 steps, as specified."""
     prob = W.config_sphere_ag_48()

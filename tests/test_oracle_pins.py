@@ -26,9 +26,9 @@ H_OFF = ((0, 1, 1), (1, 0, 1), (1, 1, 0))
 z = Poly([0.0, 1.0])
 
 
-def periodic_problem(n3, dx, courant=0.5, materials=()):
+def periodic_problem(n3, dx, courant=0.5, materials=(), eps_b=1.0):
     return {"shape": tuple(n3), "dx": dx, "courant": courant, "pml": 0, "bc": ("periodic",) * 3,
-            "eps_b": 1.0, "materials": list(materials), "shapes": [], "source": None, "monitors": None}
+            "eps_b": eps_b, "materials": list(materials), "shapes": [], "source": None, "monitors": None}
 
 
 def positions(off, n3):
@@ -65,10 +65,13 @@ def roots_u_to_omega(poly, dt):
 
 # --------------------------------------------------------------- Yee / CFL
 
-def test_vacuum_oblique_plane_wave_matches_discrete_dispersion():
-    """Exact discrete plane wave: sin^2(w dt/2) = S^2 sum_a sin^2(k_a dx/2),
-    H = K x E / (mu0 Omega) with the discrete wave vector K and frequency Omega."""
-    n3, dx, S = (16, 12, 10), 1e-8, 0.5
+@pytest.mark.parametrize("eps_b,S", [(1.0, 0.5), (1.77, 0.45)])
+def test_vacuum_oblique_plane_wave_matches_discrete_dispersion(eps_b, S):
+    """Exact discrete plane wave in a background of relative permittivity
+    eps_b: sin^2(w dt/2) = (S^2 / eps_b) sum_a sin^2(k_a dx/2),
+    H = K x E / (mu0 Omega) with the discrete wave vector K and frequency Omega
+    (Faraday's law; Ampere's with eps0 eps_b then fixes the dispersion)."""
+    n3, dx = (16, 12, 10), 1e-8
     m = np.array([1, 2, 1])
     k = 2 * np.pi * m / (np.array(n3) * dx)
     s = np.sin(k * dx / 2)
@@ -76,10 +79,10 @@ def test_vacuum_oblique_plane_wave_matches_discrete_dispersion():
     e = np.array([Kt[1], -Kt[0], 0.0])
     e /= np.linalg.norm(e)
     dt = S * dx / C0
-    w = 2 / dt * math.asin(S * math.sqrt(np.sum(s ** 2)))
+    w = 2 / dt * math.asin(S * math.sqrt(np.sum(s ** 2) / eps_b))
     Om = 2 / dt * math.sin(w * dt / 2)
     h = np.cross(Kt, e) / (MU0 * Om)
-    sim = oracle.Sim(periodic_problem(n3, dx, S))
+    sim = oracle.Sim(periodic_problem(n3, dx, S, eps_b=eps_b))
     for c in range(3):
         x, y, zz = positions(E_OFF[c], n3)
         sim.array("E" + "xyz"[c])[:] = e[c] * np.cos(k[0] * x * dx + k[1] * y * dx + k[2] * zz * dx)
@@ -374,11 +377,13 @@ def test_ampere_law_holds_and_pekar():
 
 # ------------------------------------------------------------ TF/SF, CPML
 
-def test_tfsf_no_leakage_without_scatterer():
-    """Axis-aligned incidence with a matched 1D grid: the scattered-field region
-    stays empty up to rounding."""
+@pytest.mark.parametrize("eps_b,S", [(1.0, 0.5), (1.77, 0.45)])
+def test_tfsf_no_leakage_without_scatterer(eps_b, S):
+    """Axis-aligned incidence with a matched 1D grid (same background, same
+    Courant number): the scattered-field region stays empty up to rounding."""
     prob = W.small_sphere(n=36, steps=0)
     prob["shapes"] = []
+    prob["eps_b"], prob["courant"] = eps_b, S
     prob["monitors"] = None
     prob["dx"] = 1e-9
     src = dict(prob["source"])
