@@ -101,3 +101,45 @@ def test_unstable_instance_is_isolated():
         runs[q].sync()
         errs = vec_err(fields(runs[q]), ref_f[q])
         assert max(errs.values()) <= 1e-6, (q, errs)
+
+
+def edge_instances():
+    """Geometries at the edges of the tiling and the TF/SF surface: a grid
+    narrower than one tile with the TF surface one cell from every PEC wall,
+    a CPML on one axis beside PEC walls with a one-plane z chunk, and a
+    dielectric background at another Courant number."""
+    def early(q):
+        src = W.gaussian_source(q["source"]["tf_lo"], q["source"]["tf_hi"], (1.0, 9.0))
+        src["t0"] = 2.5 * src["tau"]
+        q["source"] = src
+        return q
+
+    out = []
+    q = W.small_sphere(n=36, steps=0, nf=4, K=4)
+    q.update(shape=(13, 11, 18), pml=0, bc=("pec",) * 3, monitors=None,
+             shapes=[W.sphere_shape((13, 8, 18), 2, 1)])
+    q["source"]["tf_lo"], q["source"]["tf_hi"] = (1, 1, 1), (12, 10, 17)
+    out.append(early(q))
+    q = W.small_sphere(n=36, steps=0, nf=4, K=4)
+    q.update(shape=(40, 44, 17), pml=6, bc=("pec", "cpml", "pec"), monitors=None,
+             shapes=[W.sphere_shape((40, 44, 17), 6, 1)])
+    q["source"]["tf_lo"], q["source"]["tf_hi"] = (2, 7, 2), (37, 36, 14)
+    out.append(early(q))
+    q = W.small_sphere(n=36, steps=0, nf=4, K=4)
+    q["eps_b"], q["courant"], q["monitors"] = 1.77, 0.45, None
+    out.append(early(q))
+    return out
+
+
+def test_batched_edge_geometries_match_oracle():
+    probs = edge_instances()
+    batch = [nlfdtd.Solver(p) for p in probs]
+    steps = [400, 400, 400]
+    assert nlfdtd.batch_run(batch, steps) == [0, 0, 0]
+    for p, s in zip(probs, batch):
+        s.sync()
+        o = oracle.Sim(p)
+        o.step(400)
+        ref = {c: o.array(c) for comps in VECTORS.values() for c in comps}
+        errs = vec_err(fields(s), ref)
+        assert max(errs.values()) <= 1e-4, (p["shape"], errs)
