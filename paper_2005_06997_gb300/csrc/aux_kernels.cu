@@ -147,7 +147,7 @@ __global__ void k_dft_phase(const DftParams d, int count)
 // One flush of the running DFT: block = ACC_NT frequencies x ACC_NCH chunks
 // of RCH records (accum_block).
 template <int B, int RCH>
-__global__ void __launch_bounds__(ACC_NT) k_dft_accum(const DftParams d)
+__global__ void __launch_bounds__(ACC_NT, 4) k_dft_accum(const DftParams d)
 {
     __shared__ AccShared<B, RCH> sm;
     accum_block<B, RCH>(d, (long long)blockIdx.x * RCH * ACC_NCH, ACC_NCH, blockIdx.y * ACC_NT, sm);

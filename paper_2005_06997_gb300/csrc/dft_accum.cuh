@@ -6,8 +6,11 @@
 // block of samples, FP64 accumulation.  The block stages the samples and the
 // E phases (cos, sin of w n dt) in shared memory; the H sum, whose phase is
 // w (n - 1/2) dt, is taken with the E phases and turned by exp(-i w dt / 2)
-// once per record.  The FP64 accumulators are read for G records before any
-// is written back, so that G read-modify-writes are in flight per thread.
+// once per record.  On this part FP64 runs at a small fraction of the FP32
+// rate and bounds the flush, so FP64 is kept to the accumulator additions.
+// The FP64 accumulators are read for G records before any is written back,
+// so that G read-modify-writes are in flight per thread.  The sample rows
+// (RCH floats per sample) start on 16-byte boundaries.
 #pragma once
 
 #include "nlf_internal.h"
@@ -18,18 +21,24 @@ constexpr int ACC_NT = 128;   // frequencies (threads) per block
 constexpr int ACC_NCH = 8;    // record chunks per block of a single grid
 
 template <int B, int RCH>
-struct AccShared {
+struct alignas(16) AccShared {
     float sE[B][RCH];
     float sH[B][RCH];
     float2 ph[B][ACC_NT];
 };
 
-// G records at a time of one chunk at frequency f (thread t of the block).
+// G = 4 records at a time of one chunk at frequency f (thread t of the
+// block).  The sample loop is outside the record loop, so each phase is read
+// from shared memory once per G records, and the G records' samples arrive
+// as broadcast float4 loads; every record still sums its samples in order
+// s = 0 .. B-1.  Records past the chunk's end hold zero samples and are not
+// stored.
 template <int B, int RCH>
-__device__ __forceinline__ void accum_chunk(const DftParams& d, long long r0, int f, int t, double cr, double sr,
+__device__ __forceinline__ void accum_chunk(const DftParams& d, long long r0, int f, int t, float cr, float sr,
                                             const AccShared<B, RCH>& sm)
 {
-    constexpr int G = 8;
+    constexpr int G = 4;
+    static_assert(RCH % G == 0, "record chunk must hold whole groups");
     const int rmax = (int)min((long long)RCH, d.nrec + 1 - r0);
     for (int g = 0; g < rmax; g += G) {
         double2 ae[G], ah[G];
@@ -41,25 +50,34 @@ __device__ __forceinline__ void accum_chunk(const DftParams& d, long long r0, in
                 ah[u] = d.accH[o];
             }
         }
+        float er[G], ei[G], hr[G], hi[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) er[u] = ei[u] = hr[u] = hi[u] = 0.f;
+#pragma unroll 8
+        for (int s = 0; s < B; ++s) {
+            const float2 p = sm.ph[s][t];
+            const float4 e4 = *reinterpret_cast<const float4*>(&sm.sE[s][g]);
+            const float4 h4 = *reinterpret_cast<const float4*>(&sm.sH[s][g]);
+            const float e[G] = {e4.x, e4.y, e4.z, e4.w}, h[G] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                er[u] = fmaf(e[u], p.x, er[u]);
+                ei[u] = fmaf(e[u], p.y, ei[u]);
+                hr[u] = fmaf(h[u], p.x, hr[u]);
+                hi[u] = fmaf(h[u], p.y, hi[u]);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             if (g + u < rmax) {
-                const int rr = g + u;
-                float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
-#pragma unroll
-                for (int s = 0; s < B; ++s) {
-                    const float2 p = sm.ph[s][t];
-                    const float e = sm.sE[s][rr], h = sm.sH[s][rr];
-                    er = fmaf(e, p.x, er);
-                    ei = fmaf(e, p.y, ei);
-                    hr = fmaf(h, p.x, hr);
-                    hi = fmaf(h, p.y, hi);
-                }
-                const long long o = (r0 + rr) * d.nf + f;
-                ae[u].x += (double)er;
-                ae[u].y += (double)ei;
-                ah[u].x += cr * (double)hr + sr * (double)hi;
-                ah[u].y += cr * (double)hi - sr * (double)hr;
+                const long long o = (r0 + g + u) * d.nf + f;
+                ae[u].x += (double)er[u];
+                ae[u].y += (double)ei[u];
+                // the turn by exp(-i w dt / 2) acts on the FP32 block sum in FP32
+                // (its rounding is that of the sum itself); only the two
+                // additions to the accumulator are FP64, the slow pipe here
+                ah[u].x += (double)fmaf(cr, hr[u], sr * hi[u]);
+                ah[u].y += (double)fmaf(cr, hi[u], -sr * hr[u]);
                 d.accE[o] = ae[u];
                 d.accH[o] = ah[u];
             }
@@ -87,6 +105,7 @@ __device__ __forceinline__ void accum_block(const DftParams& d, long long rb, in
     const int f = f0 + t;
     double sr = 0.0, cr = 1.0;
     if (f < d.nf) sincos(0.5 * d.omega[f] * d.dt, &sr, &cr);
+    const float crf = (float)cr, srf = (float)sr;
     const long long nr = d.nrec + 1;
     for (int ch = 0; ch < nchunk; ++ch) {
         const long long r0 = rb + (long long)ch * RCH;
@@ -99,7 +118,7 @@ __device__ __forceinline__ void accum_block(const DftParams& d, long long rb, in
             sm.sH[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
         }
         __syncthreads();
-        if (f < d.nf) accum_chunk<B, RCH>(d, r0, f, t, cr, sr, sm);
+        if (f < d.nf) accum_chunk<B, RCH>(d, r0, f, t, crf, srf, sm);
     }
 }
 }  // namespace nlf
