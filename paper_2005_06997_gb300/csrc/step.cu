@@ -912,7 +912,12 @@ __global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_pml(const StepPara
     extern __shared__ unsigned char nlf_dyn_smem[];
     const unsigned mis = smem_u32(nlf_dyn_smem) & 127u;
     SharedPML& sm = *reinterpret_cast<SharedPML*>(nlf_dyn_smem + ((128u - mis) & 127u));
-    step_tile_of<true>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
+    // z chunks in the order 0, n-1, 1, n-2, ...: the first and last chunks,
+    // CPML tiles only, start first, and the blocks left at the end are the
+    // few CPML tiles of middle chunks, which share the SMs with background
+    // tiles instead of running as an under-filled tail
+    const int zb = (int)blockIdx.z, nzb = (int)gridDim.z;
+    step_tile_of<true>(p, blockIdx.x, blockIdx.y, (zb & 1) ? nzb - 1 - (zb >> 1) : (zb >> 1), kz, sm);
 }
 
 // ---------------------------------------------------------------- batched
