@@ -244,6 +244,34 @@ def test_dielectric_background_and_another_courant_number():
         assert np.max(err) <= TOL_SIGMA, (key, np.max(err))
 
 
+def test_raised_cosine_source_in_the_n13_background():
+    """The EELS-comparison set-up of Sec. V on a small grid: a nonlocal
+    silver-like sphere with beta^2 = v_F^2 / 3, a background of index 1.3 and
+    the raised-cosine pulse with the printed w_max (values from
+    tests/golden/); fields, FP64 accumulators and cross sections against the
+    oracle."""
+    from test_oracle_golden import golden
+    s = golden("silver_sphere_setup.txt")
+    w_max = golden("raised_cosine_source.txt")["w_max_rad_s"]
+    beta = math.sqrt(s["beta_squared_over_vF_squared"]) * s["fermi_velocity_m_s"]
+    prob = W.small_sphere(n=36, steps=0, nf=16, K=4, band_ev=(1.0, 8.0),
+                          material=W.drude_material(9.0, 0.1, beta=beta))
+    prob["eps_b"] = s["background_index"] ** 2
+    src = prob["source"]
+    prob["source"] = W.raised_cos_source(src["tf_lo"], src["tf_hi"], w_max=w_max)
+    g, o = run_pair(prob, 1500, block_b=16)
+    assert_fields_match(g, o)
+    aEg, aHg = g.dft()
+    aEo, aHo = o.dft()
+    assert rel_l2(aEg, aEo) < 1e-4
+    assert rel_l2(aHg, aHo) < 1e-4
+    sg, so = g.spectra(), o.spectra()
+    sel = so["inc"] >= 1e-3 * so["inc"].max()
+    for key in ("ext", "abs", "sca"):
+        err = np.abs(sg[key][sel] - so[key][sel]) / np.max(np.abs(so[key][sel]))
+        assert np.max(err) <= TOL_SIGMA, (key, np.max(err))
+
+
 def test_sphere_ag_48_configuration():
     """The 48^3 Ag-like sphere configuration, 1000 steps, as specified."""
     prob = W.config_sphere_ag_48()
