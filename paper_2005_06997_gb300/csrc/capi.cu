@@ -33,6 +33,7 @@ long long tfsf_items(const StepParams& p);
 void launch_tfsf(const StepParams& p, cudaStream_t st);
 void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st);
 void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
+void launch_post(const StepParams& p, long long n_sites, cudaStream_t st);
 void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, uint32_t* site_q, const SiteGeom& g,
                       unsigned long long* count, cudaStream_t st);
 void launch_voxelise(const VoxParams& v, cudaStream_t st);
@@ -128,7 +129,7 @@ struct nlf_ctx {
     cudaEvent_t done = nullptr;
     cudaStream_t cap = nullptr;         // private stream for graph capture
     cudaStream_t aux = nullptr;         // second stream of the step: the CPML tiles
-    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     long long n = 0;                    // time index
@@ -804,8 +805,6 @@ int ensure_ready(nlf_ctx* c, cudaStream_t st)
     if (!c->aux) CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     if (!c->join) CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
-    if (!c->fork2) CK(cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming));
-    if (!c->join2) CK(cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming));
     return initialise(c, st);
 }
 
@@ -833,20 +832,14 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
 
 // The work after the EM step of time step n: the TF/SF corrections and the
 // material update touch disjoint cells (material sites lie two cells inside
-// the TF surface), so with both present the corrections run on the second
-// stream beside the material update.
+// the TF surface), so with both present one kernel does both.
 void launch_post(nlf_ctx* c, cudaStream_t st)
 {
     const nlf::StepParams& sp = c->sp[c->n & 1];
     const bool tf = nlf::tfsf_items(sp) > 0, met = c->n_msites > 0;
     if (tf && met) {
-        cudaEventRecord(c->fork2, st);
-        cudaStreamWaitEvent(c->aux, c->fork2, 0);
-        nlf::launch_tfsf(sp, c->aux);
-        nlf::launch_metal(sp, c->n_msites, st);
-        cudaEventRecord(c->join2, c->aux);
-        cudaStreamWaitEvent(st, c->join2, 0);
-        c->launches += 2;
+        nlf::launch_post(sp, c->n_msites, st);
+        c->launches += 1;
     } else if (tf) {
         nlf::launch_tfsf(sp, st);
         c->launches += 1;
@@ -1766,8 +1759,6 @@ void nlf_destroy(nlf_ctx* c)
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
-    if (c->fork2) cudaEventDestroy(c->fork2);
-    if (c->join2) cudaEventDestroy(c->join2);
     if (c->owned && c->base) cudaFree(c->base);
     delete c;
 }

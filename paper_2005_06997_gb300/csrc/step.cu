@@ -16,11 +16,13 @@
 // clear of the CPML slabs they run plain Yee arithmetic with no per-cell
 // tests; CPML tiles run in their own kernel (more shared memory: the psi
 // staging area) concurrently with the others.  The TF/SF connection is a
-// separate small kernel (k_tfsf) of additive corrections on the TF surface.
+// set of additive corrections on the TF surface applied after the step.
 //
-// The material update (k_metal): one thread per material E-site of a
-// compact list rewrites E^{n+1} there from the H^{n+1/2} just written and
-// advances P_CP and P_f.
+// The material update: one thread per material E-site of a compact list
+// rewrites E^{n+1} there from the H^{n+1/2} just written and advances P_CP
+// and P_f.  With a source and a material present, one kernel (k_post) runs
+// both the corrections and the material update; otherwise k_tfsf or
+// k_metal runs alone.
 //
 // f2/f3/f4 are applied in increment form, algebraically identical to the
 // paper's printed recurrences (Eq. NonlocalUpdate, Eq. GNORUpdate,
@@ -1070,6 +1072,23 @@ __global__ void __launch_bounds__(256) k_tfsf(const StepParams p, long long n)
     if (t < n) tfsf_item(p, t);
 }
 
+// The material update and the TF/SF corrections in one launch: blocks below
+// nb_metal take material sites, the rest TF/SF items.  The two touch disjoint
+// cells (material sites lie at least two cells inside the TF surface), so no
+// order between them is needed, and the short TF/SF blocks fill the SMs the
+// material blocks leave at the end of the launch.
+__global__ void __launch_bounds__(256) k_post(const StepParams p, long long n_sites, long long nb_metal, long long n_tf)
+{
+    const long long bx = blockIdx.x;
+    if (bx < nb_metal) {
+        const long long t = bx * blockDim.x + threadIdx.x;
+        if (t < n_sites) metal_entry(p, t);
+    } else {
+        const long long t = (bx - nb_metal) * blockDim.x + threadIdx.x;
+        if (t < n_tf) tfsf_item(p, t);
+    }
+}
+
 // Batched: block row y is instance y; items past that instance's count idle.
 __global__ void __launch_bounds__(256) k_tfsf_batch(const BatchStep a)
 {
@@ -1200,6 +1219,13 @@ void launch_tfsf(const StepParams& p, cudaStream_t st)
 {
     const long long n = tfsf_count(p);
     if (n > 0) k_tfsf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n);
+}
+
+void launch_post(const StepParams& p, long long n_sites, cudaStream_t st)
+{
+    const long long n_tf = tfsf_count(p);
+    const long long nb_m = (n_sites + 255) / 256, nb_t = (n_tf + 255) / 256;
+    if (nb_m + nb_t > 0) k_post<<<(unsigned)(nb_m + nb_t), 256, 0, st>>>(p, n_sites, nb_m, n_tf);
 }
 
 void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st)
