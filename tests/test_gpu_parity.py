@@ -336,6 +336,68 @@ def test_bound_state_matches_library_allocation():
 
 # ------------------------------------------------------- full-size grid
 
+# y-mirror parity of each array about the grid's centre plane: +1 even, -1 odd;
+# "node" arrays sit at integer y (index j mirrors to ny - j, j = 0 is the
+# wall), "half" arrays at y = j + 1/2 (index j mirrors to ny - 1 - j).  The
+# x-polarised, z-propagating source and a geometry centred on the plane are
+# even; H is a pseudovector, so its parities are those of E times -1.
+MIRROR_Y = {"Ex": (1, "node"), "Ey": (-1, "half"), "Ez": (1, "node"),
+            "Hx": (-1, "half"), "Hy": (1, "node"), "Hz": (-1, "half"),
+            "Px": (1, "node"), "Py": (-1, "half"), "Pz": (1, "node")}
+
+
+def mirror_pair(a, where):
+    """(a, its y-mirror image) on the indices where both exist."""
+    if where == "node":
+        return a[:, 1:, :], a[:, :0:-1, :]
+    return a, a[:, ::-1, :]
+
+
+def test_full_size_cube_tips_512_mirror_symmetry():
+    """The 512^3 cube-with-tips configuration (37 GB of state at 200
+    frequencies; 5 here) at its full size and launch shape, where the oracle
+    is out of reach: voxels and fields must have the mirror symmetry of the
+    problem about the y = 256 plane.  Voxels exactly; fields to 1e-5 (of
+    each component's norm, floored at 20 % of its vector's) after 400 steps,
+    with the pulse inside the particle."""
+    prob = W.config_cube_tips_512()
+    prob["monitors"]["omega"] = prob["monitors"]["omega"][::40]
+    src = W.gaussian_source(prob["source"]["tf_lo"], prob["source"]["tf_hi"], (1.0, 5.0))
+    src["t0"] = 0.6 * src["tau"]
+    prob["source"] = src
+    g = nlfdtd.Solver(prob)
+    try:
+        vox = g.voxels()
+        assert np.count_nonzero(vox) > 0
+        for c, where in enumerate(("node", "half", "node")):
+            a, b = mirror_pair(vox[c], where)
+            assert np.array_equal(a, b), c
+        del vox
+        g.run(400)
+        g.sync()
+        num, den = {}, {}
+        for name, (sign, where) in MIRROR_Y.items():
+            f = g.field(name)
+            a, b = mirror_pair(f, where)
+            num[name] = den[name] = 0.0
+            for z0 in range(0, f.shape[0], 64):
+                da = a[z0:z0 + 64].astype(np.float64)
+                db = b[z0:z0 + 64].astype(np.float64)
+                num[name] += float(np.sum((da - sign * db) ** 2))
+                den[name] += float(np.sum(da ** 2))
+            del f, a, b
+    finally:
+        g.close()
+    # each component against max(its norm, 20 % of its vector field's norm),
+    # as in the parity bar above
+    for comps in VECTORS.values():
+        vnorm = math.sqrt(sum(den[c] for c in comps))
+        assert vnorm > 0.0, comps
+        for c in comps:
+            err = math.sqrt(num[c]) / max(math.sqrt(den[c]), COMPONENT_FLOOR * vnorm)
+            assert err <= 1e-5, (c, err)
+
+
 def test_full_size_au_gnor_224_grid():
     """The 224^3 GNOR + pole configuration's grid, geometry and launch shape,
     with a pulse that reaches the sphere within the run; every field against
