@@ -325,9 +325,9 @@ int nlf_get_info(nlf_ctx* ctx, nlf_info* info);
 /* Measurement: advance `steps` time steps with CUDA events recorded around
  * each kernel (the steps are captured and replayed once as a CUDA graph on
  * cuda_stream, as nlf_run executes them), wait, and return the summed device
- * durations in ms: ms_out[0] EM step kernels, ms_out[1] material update,
- * ms_out[2] running-DFT kernels.  The solution advances exactly as with
- * nlf_run.  The paper has no counterpart.
+ * durations in ms: ms_out[0] EM step kernels, ms_out[1] material update and
+ * TF/SF corrections, ms_out[2] running-DFT kernels.  The solution advances
+ * exactly as with nlf_run.  The paper has no counterpart.
  * Errors: NLF_E_ARG (steps < 1 or > 65536, null ms_out), NLF_E_CUDA. */
 int nlf_time_kernels(nlf_ctx* ctx, long long steps, void* cuda_stream, double* ms_out);
 long long nlf_kernel_launches(const nlf_ctx* ctx);
