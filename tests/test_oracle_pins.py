@@ -497,3 +497,64 @@ def test_voxeliser_sphere_volume():
         assert abs(np.count_nonzero(mp[c]) / vol - 1.0) < 0.02
     # the three components see the same sphere up to the cyclic relabelling
     assert np.count_nonzero(mp[0]) == np.count_nonzero(mp[1]) == np.count_nonzero(mp[2])
+
+
+# ------------------------------------------------------------------- energy
+
+def discrete_energy_series(mat, steps, n=10, dx=0.5e-9, seed=7):
+    """Metal-filled PEC box, random initial E (tangential E zero on the walls),
+    H = P = 0, no source.  Per step: the electromagnetic energy
+    eps0 eps_inf |E^n|^2 / 2 + mu0 H^{n-1/2}.H^{n+1/2} / 2 (the quantity the Yee
+    scheme conserves in vacuum) plus the free-electron kinetic energy
+    |J^{n+1/2}|^2 / (2 eps0 wp^2) with J^{n+1/2} = (P^{n+1} - P^n)/dt and the
+    pressure energy beta^2 (div P^n)(div P^{n+1}) / (2 eps0 wp^2), summed over
+    the sites (the continuum energy of Eq. NonlocDrude; uniform cells, so the
+    cell volume is left out)."""
+    n3 = (n, n, n)
+    prob = {"shape": n3, "dx": dx, "courant": 0.5, "pml": 0, "bc": ("pec",) * 3, "eps_b": 1.0,
+            "materials": [mat], "shapes": [], "source": None, "monitors": None}
+    sim = oracle.Sim(prob, all_metal(n3))
+    rng = np.random.default_rng(seed)
+    for c in "xyz":
+        sim.array("E" + c)[:] = rng.standard_normal(sim.shape3)
+    sim.array("Ex")[:, 0, :] = 0
+    sim.array("Ex")[0, :, :] = 0
+    sim.array("Ey")[:, :, 0] = 0
+    sim.array("Ey")[0, :, :] = 0
+    sim.array("Ez")[:, :, 0] = 0
+    sim.array("Ez")[:, 0, :] = 0
+    wp2, beta, dt, eps_inf = mat["wp"] ** 2, mat["beta"], sim.dt, mat["eps_inf"]
+    H0 = [np.array(sim.array("H" + c)) for c in "xyz"]
+    P0 = [np.array(sim.array("P" + c)) for c in "xyz"]
+    d0 = sim.density()
+    out = np.empty(steps)
+    for s in range(steps):
+        E = [np.array(sim.array("E" + c)) for c in "xyz"]
+        sim.step(1)
+        H1 = [np.array(sim.array("H" + c)) for c in "xyz"]
+        P1 = [np.array(sim.array("P" + c)) for c in "xyz"]
+        d1 = sim.density()
+        w = 0.5 * EPS0 * eps_inf * sum(np.sum(e * e) for e in E)
+        w += 0.5 * MU0 * sum(np.sum(a * b) for a, b in zip(H0, H1))
+        w += 0.5 * sum(np.sum(((a - b) / dt) ** 2) for a, b in zip(P1, P0)) / (EPS0 * wp2)
+        w += 0.5 * beta ** 2 * np.sum(d0 * d1) / (EPS0 * wp2)
+        out[s] = w
+        H0, P0, d0 = H1, P1, d1
+    return out
+
+
+@pytest.mark.parametrize("case", ["lossless", "lossy", "gnor"])
+def test_energy_bounded_without_loss_and_decaying_with_it(case):
+    """Without damping (gamma = D = 0) the energy of the coupled system stays
+    where it started (averaged over windows of 500 steps, within 0.1 %; a
+    growing mode, e.g. a coupling of the wrong sign, fails this); with gamma
+    (and with the GNOR diffusion term) it decreases from window to window."""
+    gamma, diff = {"lossless": (0.0, 0.0), "lossy": (0.3, 0.0), "gnor": (0.3, 1.9e-4)}[case]
+    mat = W.drude_material(9.0, gamma, beta=1.07e6, diff=diff)
+    w = discrete_energy_series(mat, 8000)
+    win = w.reshape(-1, 500).mean(axis=1)
+    if case == "lossless":
+        assert np.max(np.abs(win / win[0] - 1)) < 1e-3
+    else:
+        assert np.all(np.diff(win) < 0)
+        assert win[-1] < 0.9 * win[0]
