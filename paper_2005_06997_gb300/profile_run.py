@@ -3,7 +3,8 @@ taken on: ``python -m paper_2005_06997_gb300.profile_run <workload> <steps> [nf]
 [pec] [nosource] [nometal]``).
 
 It configures the problem through the C ABI, runs `steps` time steps, reads
-the spectra and prints the launch count.  The kernels and the problem are the
+the spectra and prints the launch count.  The name ``batched64`` runs the
+64-instance batched configuration through nlf_batch_run instead.  The kernels and the problem are the
 benchmark's; only the number of time steps and, if given, the number of DFT
 frequencies (every nf-th of the 200, to keep a profiler's memory save/restore
 small; the time-step kernel does not depend on it) differ.  The words pec,
@@ -18,10 +19,30 @@ from . import nlfdtd
 from . import workloads as W
 
 
+def run_batched(n, steps):
+    """The seeded batched configuration (n sphere / dimer solves on uneven
+    grids) advanced together by nlf_batch_run for `steps` time steps."""
+    solvers = [nlfdtd.Solver(p) for p in W.batched_instances(n=n)]
+    try:
+        status = nlfdtd.batch_run(solvers, [steps] * n)
+        for s in solvers:
+            s.sync()
+        launches = sum(s.launches for s in solvers)
+        cells = sum(s.info()["cells"] for s in solvers)
+        print("batched %d instances: %d steps, status %s, %d kernel launches counted over the contexts, %.1f M cells"
+              % (n, steps, "ok" if not any(status) else status, launches, cells / 1e6))
+    finally:
+        for s in solvers:
+            s.close()
+
+
 def main():
     name = sys.argv[1] if len(sys.argv) > 1 else "sphere_au_gnor_r10nm_224"
     steps = int(sys.argv[2]) if len(sys.argv) > 2 else 20
     torch.cuda.set_device(0)
+    if name == "batched64":
+        run_batched(64, steps)
+        return
     prob = W.CONFIGS[name]()
     if len(sys.argv) > 3:
         nf = int(sys.argv[3])
