@@ -212,13 +212,13 @@ nlf::MatCoef make_coef(const nlf_ctx* c, const nlf_material& m)
     double den = m.eps_inf, cE = 0.0;
     if (m.wp > 0.0) {
         const double Dd = m.gamma / (2.0 * dt) + 1.0 / (dt * dt);
-        const double D2 = (m.gamma / (2.0 * dt) - 1.0 / (dt * dt)) / Dd;
+        const double g2 = (m.gamma / dt) / Dd;                          // 1 + D2
         const double D3 = m.wp * m.wp / (4.0 * Dd);                    // D3 / eps0
         const double eta = m.beta * m.beta + m.diff * m.gamma;
         const double DG1 = eta / Dd, DG2 = m.diff / (2.0 * dt * Dd);
         k.free_e = 1;
         k.gnor = m.diff > 0.0;
-        k.D2 = (float)D2;
+        k.g2 = (float)g2;
         k.D3 = (float)D3;
         k.DG2 = (float)(DG2 / dx2);
         k.G = (float)((DG1 + 3.0 * DG2) / dx2);
@@ -230,11 +230,11 @@ nlf::MatCoef make_coef(const nlf_ctx* c, const nlf_material& m)
         const double A = m.A[p], Om = m.Omega[p], Ga = m.Gamma[p], ph = m.phi[p];
         const double W2 = Om * Om + Ga * Ga;
         const double Cp = Ga / dt + 1.0 / (dt * dt) + W2 / 4.0;
-        const double C2 = (Ga / dt - 1.0 / (dt * dt) - W2 / 4.0) / Cp;
+        const double c2g = (2.0 * Ga / dt) / Cp;                        // 1 + C2
         const double C4 = A * Om * (Om * std::cos(ph) - Ga * std::sin(ph)) / Cp;
         const double C3 = C4 / 2.0 - A * Om * std::sin(ph) / (dt * Cp);
         const double C5 = C4 / 2.0 + A * Om * std::sin(ph) / (dt * Cp);
-        k.C2[p] = (float)C2;
+        k.c2g[p] = (float)c2g;
         k.C3[p] = (float)C3;
         k.C4[p] = (float)C4;
         k.C5[p] = (float)C5;

@@ -36,9 +36,13 @@ struct MatCoef {
     float inv_den;      // 1 / (eps_inf + D3 + sum C3)
     float cE;           // 3 D3 + sum (C3 + C4)
     float G;            // (D_G1 + 3 D_G2) / dx^2  (D_NL / dx^2 for the nonlocal Drude model)
-    float D2, D3, DG2;  // D2; D3/eps0; D_G2/dx^2
-    float C2[NLF_MAX_POLES], C3[NLF_MAX_POLES], C4[NLF_MAX_POLES], C5[NLF_MAX_POLES],
-        kap[NLF_MAX_POLES];   // C3..C5 / eps0; kap = (Om^2 + Ga^2) / Cp
+    // g2 = 1 + D2 and c2g = 1 + C2, formed without cancellation in FP64
+    // (gamma dt / (1 + gamma dt / 2) and its pole analogue): D2 and C2 lie
+    // within gamma dt of -1, so as FP32 numbers they would carry the damping
+    // with only a few significant digits
+    float g2, D3, DG2;  // 1 + D2; D3/eps0; D_G2/dx^2
+    float c2g[NLF_MAX_POLES], C3[NLF_MAX_POLES], C4[NLF_MAX_POLES], C5[NLF_MAX_POLES],
+        kap[NLF_MAX_POLES];   // 1 + C2; C3..C5 / eps0; kap = (Om^2 + Ga^2) / Cp
     int free_e;         // has free electrons (P_f is updated)
     int gnor;           // D > 0: GD history used
     int npoles;

@@ -36,6 +36,9 @@
 //   E^{n+1} = E^n + delta,
 //   delta (eps_inf + D3 + C3) = S curl Ht - a_f - a_c - (D_G1 + 3 D_G2) GD - (3 D3 + C3 + C4) E^n
 // (the last line carries the -C4 of substituting f3 into Ampere's law).
+// D2 and C2 enter as -D2 dP = dP - (1 + D2) dP with 1 + D2 (and 1 + C2)
+// stored in FP32 to full relative precision, so the damping they carry is
+// not rounded away.
 // GD^n = grad(div P_f^n) is evaluated as the difference of node divergences,
 // which equals Eq. GradDiv term by term.
 //
@@ -236,7 +239,7 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
         p.P1[C][b] = p_old + dP;
-        float a_new = -m.D2 * dP + m.D3 * En;
+        float a_new = fmaf(-m.g2, dP, dP) + m.D3 * En;      // -D2 dP + D3 E^n
         if (m.gnor) {
             a_new += m.DG2 * (g1 - 4.f * gd);
             p.gdp[C][b] = gd;
@@ -249,7 +252,7 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
         const float dPc = ac[pp] + m.C3[pp] * (En + delta) + m.C4[pp] * En;
         const float pcn = pc[pp] + dPc;
         p.pcp[pp][C][b] = pcn;
-        p.auxcp[pp][C][b] = -m.kap[pp] * pcn - m.C2[pp] * dPc + m.C5[pp] * En;
+        p.auxcp[pp][C][b] = -m.kap[pp] * pcn + fmaf(-m.c2g[pp], dPc, dPc) + m.C5[pp] * En;
     }
 }
 
