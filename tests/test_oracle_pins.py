@@ -118,6 +118,32 @@ def test_cfl_bound(S, stable):
         assert e1 > 1e10 * e0
 
 
+@pytest.mark.parametrize("b,stable", [(0.999, True), (1.001, False)])
+def test_hydrodynamic_stability_bound(b, stable):
+    """The pressure term of Eq. NonlocalUpdate adds beta^2 dt^2 K^2 / 4 to
+    sin^2(w dt / 2) of a longitudinal mode (the discrete relation of the
+    longitudinal-plasmon pin); with K^2 at most 12 / dx^2 (the (1,1,1)
+    Nyquist mode of an even periodic grid, which has no curl and so no H)
+    the scheme is stable iff beta dt sqrt(3) / dx <= 1, whatever wp (the
+    (1,2,1)/4 average keeps the wp term stable).  Metal-filled periodic box,
+    random E, beta set to b dx / (sqrt(3) dt)."""
+    n3, dx = (8, 8, 8), 1e-9
+    probe = oracle.Sim(periodic_problem(n3, dx, 0.5))
+    beta = b * dx / (math.sqrt(3) * probe.dt)
+    mat = {"eps_inf": 1.0, "wp": W.ev(9.0), "gamma": 0.0, "beta": beta, "diff": 0.0}
+    sim = oracle.Sim(periodic_problem(n3, dx, 0.5, [mat]), all_metal(n3))
+    rng = np.random.default_rng(3)
+    for c in "xyz":
+        sim.array("E" + c)[:] = rng.uniform(-1, 1, size=(8, 8, 8))
+    e0 = sum(np.sum(sim.array("E" + c) ** 2) for c in "xyz")
+    sim.step(400)
+    e1 = sum(np.sum(sim.array("E" + c) ** 2) for c in "xyz")
+    if stable:
+        assert e1 < 10 * e0
+    else:
+        assert e1 > 1e10 * e0
+
+
 # ------------------------------------------------- free-electron responses
 
 def drude_lhs(dt, gamma, v=z):
