@@ -4,14 +4,17 @@
 One benchmark step is one whole solve of the workload through every step of
 the method: voxelise the geometry, build the coefficient tables, advance all
 time steps (fused H/E/P_CP/P_f update with CPML and TF/SF, running FP64 DFT on
-the flux boxes), and reduce the cross sections.  The workload is the 224^3
-Au-like GNOR sphere with a Lorentz pole (r = 10 nm, dx = 0.2 nm, 12-cell CPML,
-8000 steps, 200 frequencies); its state (~9 GB) is far larger than L2, so no
-explicit L2 flush is needed between steps.
+the flux boxes), and reduce the cross sections.  The headline workload is the
+largest single-GPU configuration: the 512^3 Au-like GNOR cube with six
+rounded pyramidal tips (60 nm cube, 3 nm apex radius, dx = 0.25 nm, 12-cell
+CPML, 10000 time steps, 1-5 eV, 200 frequencies; ~37 GB of state, far larger
+than L2, so no explicit L2 flush is needed between steps).  The 224^3 Au-like
+GNOR sphere with a Lorentz pole (8000 steps) is reported beside it under
+"workloads".
 
-  value  - Gcell-updates/s on the device (CUDA events around each solve, the
-           state already resident in HBM; nlf_reset re-voxelises and clears it)
-  e2e    - the same metric through the public API from scratch: context
+  value  - Gcell-updates/s on the device (CUDA events around the timed solves,
+           the state already resident in HBM; nlf_reset re-voxelises and clears it)
+  e2e    - the same metric through the public API from host inputs: context
            creation, host->device upload of the problem, the solve and the
            device->host read of the spectra, timed on the host
   roofline - the EM step (k_step with k_step_pml running concurrently on a
@@ -20,9 +23,12 @@ explicit L2 flush is needed between steps.
            each kernel of the last 64 time steps of each solve, replayed as
            one CUDA graph) against the measured HBM copy bandwidth; the
            material update and DFT kernels are reported beside it
+  whole_step - the whole solve's time per time step against the hot-path
+           byte count of one time step (fields, hydrodynamic state, CPML,
+           material ids, running DFT)
   cpu_baseline - the FP64 CPU oracle on a bounded sample of the same workload
-  serving - solves/s and p50/p99 latency of the seeded request stream's first
-           requests, continuous batching against one grid at a time
+  serving - solves/s and p50/p99 latency of the seeded request stream,
+           continuous batching against one grid at a time
   batched - the 64-instance batched configuration (uneven 40^3..128^3 grids,
            4000 time steps each) advanced together by nlf_batch_run, against
            the same solves run one grid per launch sequence (wall time)
@@ -46,7 +52,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "sphere_au_gnor_r10nm_224"
+HEADLINE = "cube_tips_au_gnor_512"
+SECOND = "sphere_au_gnor_r10nm_224"
+HEADLINE_SEGMENT = 1000       # time steps per benchmark step (a tenth of the headline solve)
+REF_SAMPLE_STEPS = 1          # oracle time steps per reference-arm step
+CPU_SAMPLE_STEPS = 8          # oracle time steps of the cpu_baseline sample
 METRIC = "nonlocal FDTD Gcell-updates/s"
 UNIT = "Gcell-updates/s"
 
@@ -124,6 +134,7 @@ def oracle_sample(prob, steps, gpu_check=False):
     import oracle
     oracle.build()
     s = oracle.Sim(prob)
+    s.step(1)                     # first touch of the oracle's arrays, untimed
     t0 = time.perf_counter()
     s.step(steps)
     dt = time.perf_counter() - t0
@@ -132,7 +143,7 @@ def oracle_sample(prob, steps, gpu_check=False):
     if gpu_check:
         from paper_2005_06997_gb300 import nlfdtd
         g = nlfdtd.Solver(prob)
-        g.run(steps)
+        g.run(steps + 1)
         g.sync()
         acc = {}
         for vec, comps in (("E", ("Ex", "Ey", "Ez")), ("H", ("Hx", "Hy", "Hz"))):
@@ -146,19 +157,6 @@ def oracle_sample(prob, steps, gpu_check=False):
         g.close()
     s.close()
     return cells * steps / dt / 1e9, dt, acc
-
-
-def oracle_one_thread(steps):
-    """The oracle on `steps` steps of the workload with one host thread (a
-    separate process, since the OpenMP team size is fixed at first use)."""
-    code = ("import sys, time, math; sys.path.insert(0, %r); import oracle; "
-            "from paper_2005_06997_gb300 import workloads as W; p = W.CONFIGS[%r](); s = oracle.Sim(p); "
-            "t = time.perf_counter(); s.step(%d); dt = time.perf_counter() - t; "
-            "print(math.prod(p['shape']) * %d / dt / 1e9, dt)") % (ROOT, WORKLOAD, steps, steps)
-    env = dict(os.environ, OMP_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-    v, dt = out.stdout.split()[-2:]
-    return float(v), float(dt)
 
 
 def replica_time_ms(local_ms, dist, device):
@@ -177,66 +175,146 @@ def replica_value(world, cell_updates_per_rank, job_ms):
     return world * cell_updates_per_rank / (job_ms * 1e-3) / 1e9
 
 
-def run_reference(args, rank, world):
+def host_mem_available():
+    """Bytes of host memory available now (Linux), or None."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        return None
+    return None
+
+
+def oracle_bytes(prob):
+    """Host memory the FP64 oracle holds for a problem: full-grid FP64 arrays
+    (E with two histories, H, P_f with two histories, two grad-div histories
+    and the current one, CPML psi for every component and axis, the poles'
+    three generations) plus the DFT accumulators."""
+    cells = math.prod(prob["shape"])
+    poles = max([len(m.get("poles", [])) for m in prob.get("materials", [])] + [0])
+    arrays = 9 + 3 + 9 + 9 + 18 + 9 * poles
+    nrec = 0
+    mo = prob.get("monitors")
+    if mo is not None:
+        for lo, hi in ((mo["abs_lo"], mo["abs_hi"]), (mo["sca_lo"], mo["sca_hi"])):
+            e = [h - l + 1 for l, h in zip(lo, hi)]
+            nrec += 4 * (e[0] * e[1] + e[1] * e[2] + e[0] * e[2])
+        nrec = nrec * len(mo["omega"]) * 32
+    return arrays * 8 * cells + nrec
+
+
+def baseline_workload(name):
+    """The workload the oracle can be timed on here: `name` itself when its
+    arrays fit the host's available memory (with a 25 % margin), else None."""
     from paper_2005_06997_gb300 import workloads as W
-    prob = W.CONFIGS[WORKLOAD]()
+    prob = W.CONFIGS[name]()
+    avail = host_mem_available()
+    need = oracle_bytes(prob)
+    if avail is not None and need * 1.25 > avail:
+        return None, need, avail
+    return prob, need, avail
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, created once for
+    the headline workload (its set-up untimed); each benchmark step advances
+    it REF_SAMPLE_STEPS time steps."""
     if rank != 0:
         return
-    sample_steps = prob["monitors"]["K"]
-    vals = []
-    for _ in range(args.warmup):
-        oracle_sample(prob, 2)
-    t_all = 0.0
-    for _ in range(args.steps):
-        v, dt, _ = oracle_sample(prob, sample_steps)
-        vals.append(v)
-        t_all += dt
-    value = args.steps * sample_steps * math.prod(prob["shape"]) / t_all / 1e9
+    import oracle
+    prob, need, avail = baseline_workload(HEADLINE)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if prob is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle of %s needs %.0f GB of host memory, "
+                          "%.0f GB available" % (HEADLINE, need / 1e9, (avail or 0) / 1e9)}), flush=True)
+        return
+    oracle.build()
+    sim = oracle.Sim(prob)
+    for _ in range(args.warmup):
+        sim.step(REF_SAMPLE_STEPS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(REF_SAMPLE_STEPS)
+    t_all = time.perf_counter() - t0
+    sim.close()
+    value = args.steps * REF_SAMPLE_STEPS * math.prod(prob["shape"]) / t_all / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": math.prod(prob["shape"]), "time_steps_per_step": sample_steps},
+        "config": {"workload": HEADLINE, "cells": math.prod(prob["shape"]), "time_steps_per_step": REF_SAMPLE_STEPS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "%d time steps of the %s grid per step (FP64 oracle)" % (sample_steps, WORKLOAD)},
+                         "sample": "%d time step(s) of the %s grid per step (FP64 oracle, set up once, untimed)"
+                         % (REF_SAMPLE_STEPS, HEADLINE)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, world, dist):
+def survey_step_bytes(info, prob):
+    """Algorithmic HBM bytes of one whole time step by the hot-path byte
+    count: 48 per cell (E and H read and written once, FP32), 8 (2 + g +
+    2 poles) per plasmonic E-site (P_f, a_f, the GNOR history, P_CP and a_CP
+    read and written), 32 per CPML slab cell and axis (two psi_E and two psi_H
+    read and written), 1 per bounding-box site (the material id), and the
+    running DFT: 12 bytes per record every K steps (E, H samples) and 32 bytes
+    per record and frequency per flush of B samples (FP64 accumulators read
+    and written)."""
+    mo = prob.get("monitors")
+    dft = 0.0
+    if mo is not None:
+        nf = len(mo["omega"])
+        K = mo.get("K", 16)
+        B = 32
+        nrec = info["dft_records"] + 1
+        dft = 12.0 * nrec / K + 32.0 * nrec * nf / (B * K)
+    g = 1 if info["gnor"] else 0
+    metal = 8.0 * (2 + g + 2 * info["n_poles"]) * info["metal_sites"] + 3.0 * info["bbox_cells"]
+    return 48.0 * info["cells"] + 32.0 * info["pml_slab_cells"] + metal + dft
+
+
+def measure(name, n_steps, n_warmup, dist, dev, stream, e2e_reps, seg=None, tail=64):
+    """Device-timed solves of workload `name` (state resident in HBM).  One
+    benchmark step is a segment of `seg` time steps (default: the whole
+    solve); a solve is steps / seg consecutive segments, the first one
+    starting with nlf_reset (clear, re-voxelise, upload the tables) and the
+    last one ending with the cross sections.  The timed region starts with a
+    fresh solve.  CUDA events around each kernel of the last `tail` time
+    steps of every solve give the per-kernel figures; the end-to-end rate is
+    taken through the C ABI from host inputs."""
     import torch
     from paper_2005_06997_gb300 import nlfdtd
     from paper_2005_06997_gb300 import workloads as W
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    prob = W.CONFIGS[WORKLOAD]()
+    prob = W.CONFIGS[name]()
     steps = prob["steps"]
+    seg = steps if seg is None else seg
+    assert steps % seg == 0 and seg > tail
+    per_solve = steps // seg
     cells = math.prod(prob["shape"])
-    stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-
     solver = nlfdtd.Solver(prob)
     solver.reset(sp)
     info = solver.info()
-    step_bytes = info["step_bytes"]
-    K = prob["monitors"]["K"]
-    tail = 64          # single-step launches at the end of each solve, timed one by one
+    out = {}
 
-    def solve(record_kernel_times=None):
-        solver.reset(sp)
-        solver.run(steps - tail, sp)
-        if record_kernel_times is not None:
-            # the last steps with CUDA events around each kernel (one captured graph)
-            record_kernel_times.append(solver.time_kernels(tail, sp))
+    def segment(pos, record_kernel_times=None):
+        if pos == 0:
+            solver.reset(sp)
+        if pos == per_solve - 1:
+            if record_kernel_times is not None:
+                solver.run(seg - tail, sp)
+                record_kernel_times.append(solver.time_kernels(tail, sp))
+            else:
+                solver.run(seg, sp)
+            out["spec"] = solver.spectra()
         else:
-            solver.run(tail, sp)
-        return solver.spectra()
+            solver.run(seg, sp)
 
-    for _ in range(args.warmup):
-        solve()
+    for w in range(n_warmup):
+        segment(w % per_solve)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -244,110 +322,184 @@ def run_ours(args, rank, world, dist):
     clocks.start()
     launches0 = solver.launches
     kernel_ev = []
-    times = []
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_stop = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for _ in range(args.steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        spec = solve(kernel_ev)
-        b.record(stream)
-        times.append((a, b))
+    for w in range(n_steps):
+        segment(w % per_solve, kernel_ev)
     t_stop.record(stream)
+    launches = solver.launches - launches0
+    # finish the solve in progress (untimed) for the kernel figures and the
+    # comparison with the oracle's stored full-length run
+    w = n_steps
+    while w % per_solve:
+        segment(w % per_solve, kernel_ev)
+        w += 1
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    launches = solver.launches - launches0
+    world = dist.get_world_size() if dist is not None else 1
     total_ms = replica_time_ms(t_start.elapsed_time(t_stop), dist, "cuda")
     n_timed = tail * len(kernel_ev)
-    k_mean_ms = sum(t["step_ms"] for t in kernel_ev) / n_timed
-    m_mean_ms = sum(t["metal_ms"] for t in kernel_ev) / n_timed
-    d_mean_ms = sum(t["dft_ms"] for t in kernel_ev) / n_timed
+    k_ms = sum(t["step_ms"] for t in kernel_ev) / n_timed
+    m_ms = sum(t["metal_ms"] for t in kernel_ev) / n_timed
+    d_ms = sum(t["dft_ms"] for t in kernel_ev) / n_timed
+    golden = golden_errors(solver, name, out["spec"])
     peak, peak_kind = peaks()
-    step_kernel_bytes = info["step_kernel_bytes"]
-    metal_kernel_bytes = info["metal_kernel_bytes"]
-    achieved = step_kernel_bytes / (k_mean_ms * 1e-3) / 1e9
-    value = replica_value(world, args.steps * steps * cells, total_ms)
+    kb = info["step_kernel_bytes"]
+    mb = info["metal_kernel_bytes"]
+    sb = survey_step_bytes(info, prob)
+    ms_per_time_step = total_ms / (n_steps * seg)
+    value = replica_value(world, n_steps * seg * cells, total_ms)
+    solver.close()
 
-    # end to end through the public API: create, upload, solve, read the spectra
+    # end to end through the public API from host inputs: create, upload and
+    # voxelise, solve, read the spectra back; host clock around each
     torch.cuda.synchronize()
     e2e_times = []
     h2d = d2h = 0
-    for _ in range(max(1, min(3, args.steps))):
+    for _ in range(e2e_reps):
         t0 = time.perf_counter()
         s2 = nlfdtd.Solver(prob)
         s2.run(steps, sp)
-        sp2 = s2.spectra()
+        s2.spectra()
         t1 = time.perf_counter()
         inf2 = s2.info()
         h2d, d2h = inf2["h2d_bytes"], inf2["d2h_bytes"]
         s2.close()
         e2e_times.append(t1 - t0)
     e2e_val = steps * cells / statistics.mean(e2e_times) / 1e9 * world
-    del solver
 
-    serving = None
-    if args.serving > 0:
-        serving = run_serving(args.serving)
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(tp):
+        try:
+            with open(tp) as f:
+                tr = json.load(f)
+            ent = tr.get(name) if isinstance(tr, dict) else None
+            if ent and ent.get("kernel_hash") == kernel_hash():
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    ext = out["spec"]["ext"]
+    return {
+        "workload": name, "value": value, "ms_per_step": total_ms / n_steps, "steps": n_steps,
+        "warmup": n_warmup, "cells": cells, "time_steps_per_step": seg, "time_steps_per_solve": steps,
+        "launches": launches,
+        "grid": list(prob["shape"]), "dx_m": prob["dx"],
+        "frequencies": len(prob["monitors"]["omega"]), "state_gb": info_bytes(prob) / 1e9,
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": kb / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": kb / (k_ms * 1e-3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "EM step: k_step + k_step_pml (concurrent), per time step",
+                     "kernel_ms": k_ms, "bytes_per_launch": kb},
+        "whole_step": {"ms": ms_per_time_step, "bytes": sb,
+                       "gbs": sb / (ms_per_time_step * 1e-3) / 1e9,
+                       "frac": sb / (ms_per_time_step * 1e-3) / 1e9 / peak,
+                       "what": "whole solve time per time step (reset, voxelise, every step, DFT, spectra) "
+                               "against the hot-path byte count of one time step"},
+        "kernels_per_time_step": {
+            "em_step": {"ms": k_ms, "bytes": kb, "gbs": kb / (k_ms * 1e-3) / 1e9},
+            "k_post": {"what": "material update and TF/SF corrections (bytes: material sites)",
+                       "ms": m_ms, "bytes": mb, "gbs": mb / (m_ms * 1e-3) / 1e9 if m_ms > 0 else None},
+            "dft": {"ms": d_ms}},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "spectrum_peak_ev": float(prob["monitors"]["omega"][int(ext.argmax())] / W.EV_TO_RAD),
+        "error_vs_oracle": golden,
+    }
+
+
+def golden_errors(solver, name, spec):
+    """Errors of a finished solve against the FP64 oracle's full-length run
+    of the same problem (tests/golden/full_run_<name>.npz, written by
+    tests/golden/make_full_run_golden.py): relative L2 of each vector field
+    over the stored sample sites, relative error of each field's norm, the
+    largest error of sigma_ext where I >= 1e-3 max I relative to its largest
+    magnitude there, and the frequency index of the extinction maximum (GPU,
+    oracle)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "full_run_%s.npz" % name)
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    out = {"golden": os.path.relpath(path, ROOT)}
+    for vec in ("E", "H", "P"):
+        num = den = 0.0
+        n_got = n_ref = 0.0
+        for c in "xyz":
+            f = vec + c
+            a = solver.field(f).astype(np.float64).reshape(-1)
+            ref = g["val_" + f]
+            num += float(np.sum((a[g["idx_" + f]] - ref) ** 2))
+            den += float(np.sum(ref ** 2))
+            n_got += float(np.sum(a * a))
+            n_ref += float(g["sumsq_" + f])
+        out["rel_l2_samples_" + vec] = math.sqrt(num / den) if den > 0 else None
+        out["rel_norm_" + vec] = abs(math.sqrt(n_got) - math.sqrt(n_ref)) / math.sqrt(n_ref) if n_ref > 0 else None
+    inc = g["inc"]
+    m = inc >= 1e-3 * inc.max()
+    out["sigma_ext_rel"] = float(np.max(np.abs(spec["ext"][m] - g["ext"][m])) / np.max(np.abs(g["ext"][m])))
+    i_ref, i_got = int(np.argmax(g["ext"])), int(np.argmax(spec["ext"]))
+    out["peak_index"] = [i_got, i_ref]
+    return out
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    head = measure(HEADLINE, args.steps, args.warmup, dist, dev, stream, e2e_reps=1, seg=HEADLINE_SEGMENT)
+    second = None
+    if not args.headline_only:
+        second = measure(SECOND, max(args.steps, 5), max(args.warmup, 3), dist, dev, stream, e2e_reps=3)
+    serving = run_serving(args.serving) if args.serving > 0 else None
     batched = run_batched(args.batched) if args.batched > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = prob["monitors"]["K"]
-        v, dt, acc = oracle_sample(prob, sample, gpu_check=True)
-        cpu = {"value": v, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
-               "kind": "oracle", "sample": "%d time steps of the %s grid (FP64 oracle, %.1f s)" %
-               (sample, WORKLOAD, dt),
-               "gpu_rel_l2_vs_oracle": acc}
-        try:
-            v1, dt1 = oracle_one_thread(2)
-            cpu["one_thread"] = {"value": v1, "sample": "2 time steps, one host thread (%.1f s)" % dt1}
-        except Exception as e:              # report, do not fail the benchmark line
-            cpu["one_thread"] = {"error": str(e)[:200]}
+        prob, need, avail = baseline_workload(HEADLINE)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        if prob is None:
+            cpu = {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "not run: the FP64 oracle of %s needs %.0f GB of host memory, %.0f GB available"
+                   % (HEADLINE, need / 1e9, (avail or 0) / 1e9)}
+        else:
+            v, dt, acc = oracle_sample(prob, CPU_SAMPLE_STEPS, gpu_check=True)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d time steps of the %s grid (FP64 oracle, %.1f s after its set-up)" %
+                   (CPU_SAMPLE_STEPS, HEADLINE, dt),
+                   "gpu_rel_l2_vs_oracle": acc}
 
     if rank == 0:
-        traffic = None
-        tp = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-        if os.path.exists(tp):
-            try:
-                with open(tp) as f:
-                    tr = json.load(f)
-                if tr.get("workload") == WORKLOAD and tr.get("kernel_hash") == kernel_hash():
-                    traffic = tr["bytes_per_launch"]
-            except Exception:
-                traffic = None
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells, "time_steps_per_step": steps,
-                       "grid": list(prob["shape"]), "dx_m": prob["dx"], "frequencies": len(prob["monitors"]["omega"]),
-                       "l2": "state %.1f GB > 129 MB L2, no flush needed" % (info_bytes(prob) / 1e9),
+            "config": {"workload": HEADLINE, "cells": head["cells"], "time_steps_per_step": head["time_steps_per_step"],
+                       "time_steps_per_solve": head["time_steps_per_solve"],
+                       "step": "a segment of %d time steps; a solve is %d segments, the first re-voxelising "
+                               "and clearing the state, the last reducing the cross sections"
+                       % (head["time_steps_per_step"], head["time_steps_per_solve"] // head["time_steps_per_step"]),
+                       "grid": head["grid"], "dx_m": head["dx_m"], "frequencies": head["frequencies"],
+                       "l2": "state %.1f GB > 129 MB L2, no flush needed" % head["state_gb"],
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "EM step: k_step + k_step_pml (concurrent), per time step",
-                         "kernel_ms": k_mean_ms, "bytes_per_launch": step_kernel_bytes},
-            "kernels_per_time_step": {
-                "k_step": {"ms": k_mean_ms, "bytes": step_kernel_bytes,
-                           "gbs": step_kernel_bytes / (k_mean_ms * 1e-3) / 1e9},
-                "k_post": {"what": "material update and TF/SF corrections, one launch (bytes: material sites)",
-                           "ms": m_mean_ms, "bytes": metal_kernel_bytes,
-                           "gbs": metal_kernel_bytes / (m_mean_ms * 1e-3) / 1e9 if m_mean_ms > 0 else None},
-                "dft": {"ms": d_mean_ms},
-                "step_bytes": step_bytes},
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clk,
+            "roofline": head["roofline"],
+            "whole_step": head["whole_step"],
+            "kernels_per_time_step": head["kernels_per_time_step"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["launches"],
+            "clocks": head["clocks"],
             "cpu_baseline": cpu,
-            "spectrum_peak_ev": float(prob["monitors"]["omega"][int(spec["ext"].argmax())] / W.EV_TO_RAD),
+            "spectrum_peak_ev": head["spectrum_peak_ev"],
         }
+        if second is not None:
+            line["workloads"] = {SECOND: second}
         if serving is not None:
             line["serving"] = serving
         if batched is not None:
@@ -455,10 +607,11 @@ def kernel_hash():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the 224^3 section")
     ap.add_argument("--serving", type=int, default=48, help="requests of the serving stream to run (0: skip)")
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched configuration (0: skip)")
     args = ap.parse_args()

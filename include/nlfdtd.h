@@ -52,9 +52,11 @@ extern "C" {
 #define NLF_E_STATE       (-8)  /* call made in the wrong order */
 #define NLF_E_UNSUPPORTED (-9)  /* valid request outside what this build implements */
 
+/* Boundary of each axis: a PEC wall, or a CPML of pml_cells in front of it
+ * (the absorbing boundary of Sec. V, with the coefficients of the
+ * convolutional PML; the paper gives the thickness only). */
 #define NLF_BC_PEC       0
 #define NLF_BC_CPML      1      /* CPML of pml_cells, PEC behind it */
-#define NLF_BC_PERIODIC  2      /* reserved: nlf_create returns NLF_E_UNSUPPORTED */
 
 #define NLF_SHAPE_SPHERE     1
 #define NLF_SHAPE_BOX        2
@@ -72,6 +74,7 @@ extern "C" {
 #define NLF_FIELD_PX 6          /* free-electron polarisation P_f (Sec. III) */
 #define NLF_FIELD_PY 7
 #define NLF_FIELD_PZ 8
+#define NLF_FIELD_DENSITY 9     /* free-electron charge density div P_f at the nodes (Eq. Nsol), C/m^3 */
 
 #define NLF_MAX_POLES      4
 #define NLF_MAX_MATERIALS  32
@@ -168,9 +171,11 @@ typedef struct {
 
 typedef struct nlf_ctx nlf_ctx;
 
-/* Create a context for one grid (validates S and sizes; allocates nothing on
- * the device).  *out receives the context, to be released by nlf_destroy.
- * Errors: NLF_E_ARG, NLF_E_CFL, NLF_E_UNSUPPORTED (periodic axes). */
+/* Create a context for one grid: the Yee lattice of Table Yee with uniform
+ * cells and dt = S dx / c (Sec. III; the Courant bound S <= 1/sqrt(3) of the
+ * scheme).  Validates S and sizes; allocates nothing on the device.  *out
+ * receives the context, to be released by nlf_destroy.
+ * Errors: NLF_E_ARG (sizes, or a boundary other than PEC / CPML), NLF_E_CFL. */
 int nlf_create(const nlf_grid* grid, nlf_ctx** out);
 
 /* Material table (copied), n <= NLF_MAX_MATERIALS.  Coefficients D_1..D_d,
@@ -180,18 +185,29 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out);
 int nlf_set_materials(nlf_ctx* ctx, const nlf_material* mats, int n);
 
 /* Shapes (copied), voxelised on the device at the first run (integer,
- * bit-exact).  Replaces any material map.  Errors: NLF_E_ARG. */
+ * bit-exact): each E-site of Table Yee takes the material of the shape
+ * containing its point, with no sub-cell averaging (the staircased surfaces
+ * Sec. V discusses); P_f is carried only on those sites (the Pekar condition
+ * of Sec. III).  Replaces any material map.  Errors: NLF_E_ARG. */
 int nlf_set_shapes(nlf_ctx* ctx, const nlf_shape* shapes, int n);
 
-/* Alternative to shapes: a material id per E-site, uint8 [3][nz][ny][nx]
- * (component-major), host memory, copied.  on_device must be 0. */
+/* Alternative to shapes: a material id per E-site of Table Yee (0 =
+ * background), uint8 [3][nz][ny][nx] (component-major), copied at the call:
+ * from host memory, or from device memory if on_device (then the call
+ * synchronises the device).  Errors: NLF_E_ARG, NLF_E_STATE (after the first
+ * run), NLF_E_CUDA (device copy). */
 int nlf_set_material_map(nlf_ctx* ctx, const uint8_t* ids3, int on_device);
 
-/* Source (copied).  Errors: NLF_E_ARG, NLF_E_UNSUPPORTED (other axes). */
+/* Source (copied): the TF/SF plane wave of Sec. V, propagating along +z and
+ * polarised along x, fed by a 1D auxiliary grid; waveform per NLF_WAVE_*.
+ * Errors: NLF_E_ARG, NLF_E_UNSUPPORTED (other axes). */
 int nlf_set_source(nlf_ctx* ctx, const nlf_source* src);
 
-/* Monitors (copied, including omega).  Requires a source.  Errors: NLF_E_ARG,
- * NLF_E_GEOMETRY. */
+/* Monitors (copied, including omega): running DFTs on the faces of the two
+ * flux boxes, from which the absorption, scattering and extinction cross
+ * sections of Sec. V are formed (the paper does not say how it computes
+ * them; nlf_get_spectra states the reading).  Requires a source.
+ * Errors: NLF_E_ARG, NLF_E_GEOMETRY. */
 int nlf_set_monitors(nlf_ctx* ctx, const nlf_monitors* mon);
 
 /* Single-frequency maps on one lattice plane (Sec. V: the near-field
@@ -215,31 +231,36 @@ typedef struct {
 int nlf_set_plane_monitor(nlf_ctx* ctx, const nlf_plane_monitor* mon);
 
 /* Bytes of device state the context needs (for admission by HBM budget).
- * Valid after materials, shapes/map, source and monitors are set; 0 on error. */
+ * Valid after materials, shapes/map, source and monitors are set; 0 on error.
+ * The paper has no counterpart (its memory remark of Sec. III is about the
+ * extra grad-div history arrays GNOR needs, which this count includes). */
 size_t nlf_state_bytes(const nlf_ctx* ctx);
 
 /* Use caller-owned device memory (e.g. a torch tensor) for the whole state
- * instead of a library allocation.  dev_ptr must be 256-byte aligned and
- * stay valid until nlf_destroy.  The memory is cleared on first use.
+ * instead of a library allocation (no counterpart in the paper).  dev_ptr
+ * must be 256-byte aligned and stay valid until nlf_destroy.  The memory is cleared on first use.
  * Errors: NLF_E_ARG, NLF_E_OOM (bytes < nlf_state_bytes), NLF_E_STATE
  * (state already allocated). */
 int nlf_bind_state(nlf_ctx* ctx, void* dev_ptr, size_t bytes);
 
 /* Advance `steps` time steps on `cuda_stream` (a cudaStream_t; NULL = the
- * legacy default stream).  Asynchronous; the first call validates the
- * geometry, allocates (unless bound), voxelises and uploads.  Runs are
+ * legacy default stream): each step is f1 (H), f2 (E), f3 (P_CP), f4 (P_f) of
+ * Sec. III in that order, with the CPML, the TF/SF corrections and, every
+ * decimate_k steps, the running DFT.  Asynchronous; the first call validates
+ * the geometry (nonlocal metal only inside the total-field region, Sec. III),
+ * allocates (unless bound), voxelises and uploads.  Runs are
  * resumable: run(a) then run(b) equals run(a+b) bit for bit.
  * Errors: NLF_E_STATE, NLF_E_GEOMETRY, NLF_E_OOM, NLF_E_CUDA. */
 int nlf_run(nlf_ctx* ctx, long long steps, void* cuda_stream);
 
-/* Return the context to time index 0 on `cuda_stream` without reallocating:
- * every field, polarisation, CPML and DFT array is cleared, the tables are
- * uploaded again and the shapes voxelised again (the first call allocates,
- * like nlf_run).  Errors: as nlf_run. */
+/* Return the context to time index 0 on `cuda_stream` without reallocating
+ * (no counterpart in the paper): every field, polarisation, CPML and DFT
+ * array is cleared, the tables are uploaded again and the shapes voxelised
+ * again (the first call allocates, like nlf_run).  Errors: as nlf_run. */
 int nlf_reset(nlf_ctx* ctx, void* cuda_stream);
 
 /* Wait for the work queued by nlf_run, polling for at most timeout_ms
- * (< 0: no limit).  Checks the device error word: the non-finite watchdog
+ * (< 0: no limit; no counterpart in the paper).  Checks the device error word: the non-finite watchdog
  * (NLF_E_UNSTABLE) and the step kernel's bounded waits for its tensor-memory
  * copies (NLF_E_CUDA if one gave up; the kernel then skipped the rest of that
  * tile).  Errors: NLF_E_TIMEOUT (work still running; nothing is lost),
@@ -247,29 +268,40 @@ int nlf_reset(nlf_ctx* ctx, void* cuda_stream);
 int nlf_sync(nlf_ctx* ctx, int timeout_ms);
 
 /* Copy one field (NLF_FIELD_*) in SI units, FP32, [nz][ny][nx], to dst
- * (device memory if dst_on_device, else host).  Synchronises the context's
- * stream.  P outside the metal bounding box is zero. */
+ * (device memory if dst_on_device, else host): E^n, H^{n-1/2}, P_f^n at
+ * their Table Yee positions, or the charge density div P_f^n at the nodes
+ * (Eq. Nsol: the free-electron density change is it divided by e; backward
+ * differences P_a(node) - P_a(node - e_a) over dx).  Synchronises the
+ * context's stream.  P outside the metal bounding box is zero.
+ * Errors: NLF_E_ARG, NLF_E_STATE (no run yet), NLF_E_CUDA. */
 int nlf_get_field(nlf_ctx* ctx, int which, void* dst, int dst_on_device);
 
-/* Copy the voxelised material ids, uint8 [3][nz][ny][nx], to host dst. */
+/* Copy the voxelised material ids, uint8 [3][nz][ny][nx], to host dst (the
+ * material of every E-site of Table Yee; 0 = background).  Errors: NLF_E_ARG,
+ * and those of the first run's set-up. */
 int nlf_get_voxels(nlf_ctx* ctx, uint8_t* dst);
 
-/* Cross sections in m^2 (FP64, nf values each; any pointer may be NULL),
- * computed on the device from the FP64 accumulators:
+/* Cross sections in m^2 (FP64, nf values each; any pointer may be NULL): the
+ * absorption / scattering / extinction cross sections of Sec. V (the paper
+ * plots them but does not say how it computes them; this is the flux-box
+ * reading), computed on the device from the FP64 accumulators:
  *   sigma_abs = -(1/I) sum_abs-box (1/2) Re(E x H*).n dA,
  *   sigma_sca = +(1/I) sum_sca-box (1/2) Re(E x H*).n dA,
  *   sigma_ext = sigma_abs + sigma_sca, I = (1/2) Re(E_inc H_inc*) at the
  *   centre plane of the absorption box.  Uses library scratch in the state. */
 int nlf_get_spectra(nlf_ctx* ctx, double* s_ext, double* s_abs, double* s_sca);
 
-/* Raw accumulators, host dst of 2 * (n_records + 1) * nf * 2 doubles:
+/* Raw accumulators of the running DFT behind the cross sections of Sec. V
+ * (the e^{-i w t} convention of the Drude permittivity of Sec. II makes the
+ * kernel exp(+i w t)), host dst of 2 * (n_records + 1) * nf * 2 doubles:
  * [E | H][record][frequency][re, im], SI units, including the K dt factor.
  * Records are ordered box (absorption, scattering), normal axis a = x, y, z,
  * low face then high face, term (+E_b H_c, then -E_c H_b with (a,b,c)
  * cyclic), slower in-plane axis outer; the last record is the incident field. */
 int nlf_get_dft(nlf_ctx* ctx, double* dst);
 
-/* One plane map (nlf_set_plane_monitor): which = NLF_FIELD_EX .. EZ or
+/* One plane map (the single-wavelength near-field and density maps of
+ * Sec. V; set with nlf_set_plane_monitor): which = NLF_FIELD_EX .. EZ or
  * NLF_MAP_DENSITY; host dst of nf * n1 * n2 * 2 doubles [f][n1][n2][re, im],
  * (n1, n2) the plane's extents along its other two axes, slower first
  * (axis 0: nz, ny; axis 1: nz, nx; axis 2: ny, nx).  E in V/m s, density
@@ -277,17 +309,26 @@ int nlf_get_dft(nlf_ctx* ctx, double* dst);
  * NLF_E_CUDA. */
 #define NLF_MAP_DENSITY 9
 int nlf_get_plane_map(nlf_ctx* ctx, int which, double* dst);
+
+/* Number of flux-face records of a context with monitors (-1 otherwise). */
 long long nlf_num_records(const nlf_ctx* ctx);
 
 /* Checkpoint: copy the whole device state (nlf_state_bytes bytes, including
  * the step counter and pending DFT samples) to / from host memory.  Both
- * allocate and initialise the state first if no run has done so. */
+ * allocate and initialise the state first if no run has done so.  The paper
+ * has no counterpart (its runs of 3e5 and 4e5 iterations, Sec. V and VI, are
+ * the case for one).  Errors: NLF_E_ARG, NLF_E_CUDA. */
 int nlf_save_state(nlf_ctx* ctx, void* host);
 int nlf_load_state(nlf_ctx* ctx, const void* host);
 
-/* Advance n independent contexts, steps[i] each, in one persistent launch per
- * step group on `cuda_stream`.  status_out[i] receives each context's status
- * (NLF_OK or NLF_E_*).  All contexts must be configured. */
+/* Advance n independent contexts, steps[i] each, on `cuda_stream`: contexts
+ * on the same DFT period advance together, every kernel of a time step
+ * launched once over the concatenated work of all of them (one launch per
+ * kernel per time step, replayed from a captured CUDA graph per DFT period),
+ * the rest one context at a time.  status_out[i] receives each context's
+ * status (NLF_OK or NLF_E_*).  All contexts must be configured; contexts with
+ * a plane monitor are refused (NLF_E_ARG).  The paper has no counterpart
+ * (it runs one problem per MPI job). */
 int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* cuda_stream, int* status_out);
 
 /* Cross sections from running-DFT accumulators that the caller holds in its
@@ -307,18 +348,35 @@ int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* cuda_stre
  *   n_abs         number of absorption-box records;
  *   dA            face area of one cell, dx^2 (m^2);
  *   out           4 nf doubles: sigma_ext, sigma_abs, sigma_sca (m^2), I.
- * Asynchronous on cuda_stream.  The first call on a device looks up the
- * array's device address once for that device (make it before any stream
- * capture).  Every call shares the array, which keeps the last call's partial
- * sums (all are rewritten by each call, none needs clearing); calls that
- * overlap on the GPU race on it.  Errors: NLF_E_ARG (nf > NLF_FLUX_STATIC_PAIRS,
- * null pointers, bad sizes), NLF_E_CUDA. */
+ * The per-record weights and n_abs of a configured context are available
+ * from nlf_get_flux_weights.  Asynchronous on cuda_stream.  The first call on
+ * a device looks up the array's device address once for that device (make it
+ * before any stream capture); that address is not valid across a
+ * cudaDeviceReset of the device in the same process.  Every call shares the
+ * array, which keeps the last call's partial sums (all are rewritten by each
+ * call, none needs clearing); calls that overlap on the GPU race on it.
+ * Errors: NLF_E_ARG (nf > NLF_FLUX_STATIC_PAIRS, null pointers, bad sizes),
+ * NLF_E_CUDA (also when an earlier CUDA error is still pending on the thread:
+ * it is left pending and nothing is launched). */
 #define NLF_FLUX_STATIC_PAIRS 155648
 int nlf_flux_spectra_static(const double* acc_e, const double* acc_h, const double* coef, long long n_abs,
                             long long n_records, int nf, double dA, double* out, void* cuda_stream);
 
+/* The signed face weights of the flux records of a configured context (the
+ * record order of nlf_get_dft): host coef receives nlf_num_records doubles,
+ * each (outward sign of the face) x (sign of the term in S_a = E_b H_c -
+ * E_c H_b) x (trapezoid weight: 1/2 on the records at the face's edges
+ * along the in-plane axis other than the E component, else 1) / 2, the last
+ * factor being the 1/2 of the time-averaged Poynting vector; *n_abs receives
+ * the number of absorption-box records (they come first).  This is the flux
+ * sum of the extinction method (the cross sections of Sec. V) that
+ * nlf_get_spectra evaluates.  Host-side; no device work.  Errors: NLF_E_ARG,
+ * NLF_E_STATE (no monitors), the geometry errors of planning. */
+int nlf_get_flux_weights(nlf_ctx* ctx, double* coef, long long* n_abs);
+
 /* Time index n (E^n, H^{n-1/2} current), sizes, and number of kernels this
- * context has launched (graph replays count each kernel node). */
+ * context has launched (graph replays count each kernel node).  No
+ * counterpart in the paper. */
 long long nlf_time_index(const nlf_ctx* ctx);
 int nlf_get_info(nlf_ctx* ctx, nlf_info* info);
 
@@ -330,8 +388,13 @@ int nlf_get_info(nlf_ctx* ctx, nlf_info* info);
  * exactly as with nlf_run.  The paper has no counterpart.
  * Errors: NLF_E_ARG (steps < 1 or > 65536, null ms_out), NLF_E_CUDA. */
 int nlf_time_kernels(nlf_ctx* ctx, long long steps, void* cuda_stream, double* ms_out);
+
+/* Kernels this context has launched so far (graph replays count each kernel
+ * node).  No counterpart in the paper. */
 long long nlf_kernel_launches(const nlf_ctx* ctx);
 
+/* Text of the context's last error, and release of a context (waits for its
+ * stream, frees library-owned device memory).  No counterpart in the paper. */
 const char* nlf_last_error(const nlf_ctx* ctx);
 void nlf_destroy(nlf_ctx* ctx);
 

@@ -317,4 +317,32 @@ void launch_field_out(const float* src, float* dst, int nx, int px, long long ro
     k_field_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, nx, px, n, scale);
 }
 
+// Free-electron charge density div P_f (C/m^3) at every node (i, j, k) of the
+// grid (Eq. Nsol: n - n0 = div P_f / e), dense [nz][ny][nx]: P_a lives at the
+// E_a site half a cell up the a axis, so the node takes the backward
+// difference P_a(node) - P_a(node - e_a) along each axis over dx.  P_f is
+// stored as P/eps0 inside the metal box and is zero outside it.
+__global__ void k_density_out(const DensityParams d, float* __restrict__ dst)
+{
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const long long row = q / d.nx;
+    const int i = (int)(q - row * d.nx), j = (int)(row % d.ny), k = (int)(row / d.ny);
+    auto P = [&](int c, int ii, int jj, int kk) -> float {
+        const int bi = ii - d.bb_lo[0], bj = jj - d.bb_lo[1], bk = kk - d.bb_lo[2];
+        if (bi < 0 || bj < 0 || bk < 0 || bi >= d.bb_n[0] || bj >= d.bb_n[1] || bk >= d.bb_n[2]) return 0.f;
+        return __ldg(d.P[c] + ((long long)bk * d.bb_n[1] + bj) * d.bb_n[0] + bi);
+    };
+    const float v = (P(0, i, j, k) - P(0, i - 1, j, k)) + (P(1, i, j, k) - P(1, i, j - 1, k)) +
+                    (P(2, i, j, k) - P(2, i, j, k - 1));
+    dst[q] = (float)((double)v * d.eps0_dx);
+}
+
+void launch_density_out(const DensityParams& d, float* dst, cudaStream_t st)
+{
+    const long long n = (long long)d.nx * d.ny * d.nz;
+    k_density_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, dst);
+}
+
 }  // namespace nlf

@@ -45,6 +45,7 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
 void launch_plane_dft(const PlaneParams& m, const float* const* E, const float* const* P, const long long* step,
                       cudaStream_t st);
 void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st);
+void launch_density_out(const DensityParams& d, float* dst, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st);
@@ -1241,7 +1242,6 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out)
     if ((long long)((g.nx + 7) & ~7) * g.ny * g.nz * 3 >= (1LL << 32)) return NLF_E_ARG;
     if (g.courant > 1.0 / std::sqrt(3.0) + 1e-12) return NLF_E_CFL;
     for (int a = 0; a < 3; ++a) {
-        if (g.boundary[a] == NLF_BC_PERIODIC) return NLF_E_UNSUPPORTED;
         if (g.boundary[a] != NLF_BC_PEC && g.boundary[a] != NLF_BC_CPML) return NLF_E_ARG;
         const int n = a == 0 ? g.nx : a == 1 ? g.ny : g.nz;
         if (g.boundary[a] == NLF_BC_CPML && (g.pml_cells < 1 || 2 * g.pml_cells + 4 > n)) return NLF_E_ARG;
@@ -1298,9 +1298,16 @@ int nlf_set_shapes(nlf_ctx* c, const nlf_shape* shapes, int n)
 int nlf_set_material_map(nlf_ctx* c, const uint8_t* ids3, int on_device)
 {
     if (!c || !ids3) return NLF_E_ARG;
-    if (on_device) return fail(c, NLF_E_UNSUPPORTED, "device-resident material maps are not supported");
     if (c->ready) return fail(c, NLF_E_STATE, "geometry is fixed after the first run");
-    c->map.assign(ids3, ids3 + 3 * (size_t)c->ncell);
+    if (on_device) {
+        // the map is planned on the host (bounding box, id checks): copy it over
+        std::vector<uint8_t> h(3 * (size_t)c->ncell);
+        CK(cudaMemcpy(h.data(), ids3, h.size(), cudaMemcpyDeviceToHost));
+        c->d2h += (long long)h.size();
+        c->map.swap(h);
+    } else {
+        c->map.assign(ids3, ids3 + 3 * (size_t)c->ncell);
+    }
     c->use_map = true;
     c->shapes.clear();
     c->planned = false;
@@ -1522,7 +1529,7 @@ int nlf_sync(nlf_ctx* c, int timeout_ms)
 
 int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
 {
-    if (!c || !dst || which < 0 || which > NLF_FIELD_PZ) return NLF_E_ARG;
+    if (!c || !dst || which < 0 || which > NLF_FIELD_DENSITY) return NLF_E_ARG;
     if (!c->ready) return fail(c, NLF_E_STATE, "no state yet");
     cudaStream_t st = c->stream;
     CK(cudaStreamSynchronize(st));
@@ -1546,6 +1553,38 @@ int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
             if (scale != 1.f)
                 for (size_t q = 0; q < n; ++q) ((float*)dst)[q] *= scale;
         }
+        return NLF_OK;
+    }
+    if (which == NLF_FIELD_DENSITY) {
+        // div P_f at every node, computed on the device into dst or into a
+        // staging area of the state (the sample buffer is not large enough
+        // in general, so a host destination goes through a temporary)
+        nlf::DensityParams d{};
+        d.nx = c->g.nx;
+        d.ny = c->g.ny;
+        d.nz = c->g.nz;
+        d.eps0_dx = kEps0 / c->g.dx;
+        for (int a = 0; a < 3; ++a) {
+            d.bb_lo[a] = c->bb_lo[a];
+            d.bb_n[a] = c->has_metal ? c->bb_n[a] : 0;
+            d.P[a] = c->has_metal ? at<float>(c, c->off_P[cur]) + (size_t)a * c->nbb : nullptr;
+        }
+        float* out = (float*)dst;
+        float* tmp = nullptr;
+        if (!on_device) {
+            CK(cudaMallocAsync((void**)&tmp, n * sizeof(float), st));
+            out = tmp;
+        }
+        nlf::launch_density_out(d, out, st);
+        c->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && tmp) {
+            e = cudaMemcpyAsync(dst, tmp, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+            c->d2h += (long long)(n * sizeof(float));
+        }
+        if (tmp) cudaFreeAsync(tmp, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(c, NLF_E_CUDA, "density output: %s", cudaGetErrorString(e));
         return NLF_OK;
     }
     std::vector<float> full(n, 0.f);
@@ -1613,6 +1652,21 @@ long long nlf_num_records(const nlf_ctx* cc)
     nlf_ctx* c = const_cast<nlf_ctx*>(cc);
     if (!c || !c->have_mon || plan(c)) return -1;
     return c->nrec;
+}
+
+int nlf_get_flux_weights(nlf_ctx* c, double* coef, long long* n_abs)
+{
+    if (!c || !coef || !n_abs) return NLF_E_ARG;
+    if (!c->have_mon) return fail(c, NLF_E_STATE, "no monitors");
+    int rc = plan(c);
+    if (rc) return rc;
+    std::vector<uint32_t> re, rh, rs;
+    std::vector<double> co;
+    box_records(c, c->mon.abs_lo, c->mon.abs_hi, re, rh, rs, co);
+    box_records(c, c->mon.sca_lo, c->mon.sca_hi, re, rh, rs, co);
+    memcpy(coef, co.data(), co.size() * sizeof(double));
+    *n_abs = c->n_abs;
+    return NLF_OK;
 }
 
 int nlf_get_dft(nlf_ctx* c, double* dst)

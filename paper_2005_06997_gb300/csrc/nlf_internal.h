@@ -146,6 +146,14 @@ struct PlaneParams {
     double2* acc;               // [4][nf][n1][n2]
 };
 
+// Density output: div P_f over the whole grid from the metal box's P_f.
+struct DensityParams {
+    int nx, ny, nz;
+    int bb_lo[3], bb_n[3];
+    const float* P[3];          // P_f / eps0, [bb_n2][bb_n1][bb_n0]
+    double eps0_dx;             // eps0 / dx
+};
+
 // Where the metal box sits in the field arrays (for the site list).
 struct SiteGeom {
     int bb_lo[3], bb_n[3];

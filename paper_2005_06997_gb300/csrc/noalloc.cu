@@ -31,7 +31,11 @@ std::mutex g_sym_mu;
 double2* g_sym_ptr[kMaxDevices] = {};
 
 // Device address of the static array on the current device, looked up once
-// per device (host code only sees a stand-in for the symbol).
+// per device (host code only sees a stand-in for the symbol).  The cached
+// address belongs to the device's current context: after cudaDeviceReset (or
+// a release and re-creation of the primary context) the module is loaded
+// again and the cached address is stale, so callers that reset a device must
+// not call nlf_flux_spectra_static on it again in the same process.
 int static_scratch(double2** out)
 {
     int dev = 0;
@@ -60,11 +64,15 @@ extern "C" int nlf_flux_spectra_static(const double* acc_e, const double* acc_h,
     if (G < 1) G = 1;
     if (G > 608) G = 608;
     if (G * nf > NLF_FLUX_STATIC_PAIRS) G = NLF_FLUX_STATIC_PAIRS / nf;
+    // an error left pending by earlier, unrelated work is reported as it
+    // stands (not cleared), and nothing is launched
+    if (cudaPeekAtLastError() != cudaSuccess) return NLF_E_CUDA;
     double2* partial = nullptr;
     int rc = static_scratch(&partial);
     if (rc) return rc;
     // every partial sum is written before it is read: nothing to clear
     nlf::launch_flux(reinterpret_cast<const double2*>(acc_e), reinterpret_cast<const double2*>(acc_h), coef, n_abs,
                      n_records, nf, partial, (int)G, dA, out, (cudaStream_t)cuda_stream);
+    // nothing was pending before the launches: this is their own status
     return cudaGetLastError() == cudaSuccess ? NLF_OK : NLF_E_CUDA;
 }

@@ -18,10 +18,10 @@ from . import build as _build
 NLF_OK = 0
 ERRORS = {-1: "NLF_E_ARG", -2: "NLF_E_CFL", -3: "NLF_E_GEOMETRY", -4: "NLF_E_OOM", -5: "NLF_E_CUDA",
           -6: "NLF_E_UNSTABLE", -7: "NLF_E_TIMEOUT", -8: "NLF_E_STATE", -9: "NLF_E_UNSUPPORTED"}
-BC = {"pec": 0, "cpml": 1, "periodic": 2}
+BC = {"pec": 0, "cpml": 1}
 SHAPE = {"sphere": 1, "box": 2, "cube_tips": 3}
 WAVE = {"gaussian": 1, "raised_cos": 2}
-FIELD = {"Ex": 0, "Ey": 1, "Ez": 2, "Hx": 3, "Hy": 4, "Hz": 5, "Px": 6, "Py": 7, "Pz": 8}
+FIELD = {"Ex": 0, "Ey": 1, "Ez": 2, "Hx": 3, "Hy": 4, "Hz": 5, "Px": 6, "Py": 7, "Pz": 8, "density": 9}
 MAX_POLES = 4
 
 
@@ -93,6 +93,7 @@ SIGNATURES = {
     "nlf_get_spectra": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nlf_get_dft": (C.c_int, [_P, C.c_void_p]),
     "nlf_num_records": (C.c_longlong, [_P]),
+    "nlf_get_flux_weights": (C.c_int, [_P, C.c_void_p, C.POINTER(C.c_longlong)]),
     "nlf_save_state": (C.c_int, [_P, C.c_void_p]),
     "nlf_load_state": (C.c_int, [_P, C.c_void_p]),
     "nlf_batch_run": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(C.c_longlong), C.c_void_p,
@@ -240,7 +241,11 @@ class Solver:
         self.h = h
         mats, nm = make_materials(prob)
         _check(h, L.nlf_set_materials(h, mats, nm))
-        if material_map is not None:
+        if material_map is not None and hasattr(material_map, "data_ptr"):
+            # a device-resident map (a torch uint8 tensor on the GPU)
+            self._map = material_map
+            _check(h, L.nlf_set_material_map(h, C.c_void_p(material_map.data_ptr()), 1))
+        elif material_map is not None:
             self._map = np.ascontiguousarray(material_map, dtype=np.uint8)
             _check(h, L.nlf_set_material_map(h, self._map.ctypes.data, 0))
         else:
@@ -327,6 +332,14 @@ class Solver:
         ext, ab, sc = np.empty(nf), np.empty(nf), np.empty(nf)
         _check(self.h, self.L.nlf_get_spectra(self.h, ext.ctypes.data, ab.ctypes.data, sc.ctypes.data))
         return {"ext": ext, "abs": ab, "sca": sc}
+
+    def flux_weights(self):
+        """Signed face weights of the flux records and the absorption-box record count."""
+        nr = int(self.L.nlf_num_records(self.h))
+        coef = np.empty(nr)
+        n_abs = C.c_longlong()
+        _check(self.h, self.L.nlf_get_flux_weights(self.h, coef.ctypes.data, C.byref(n_abs)))
+        return coef, int(n_abs.value)
 
     def dft(self):
         nr = int(self.L.nlf_num_records(self.h))

@@ -67,4 +67,4 @@ def test_host_validation_without_gpu(lib):
     assert L.nlf_create(ctypes.byref(g), ctypes.byref(h)) == -2     # CFL
     g.courant = 0.5
     g.boundary[0] = 2
-    assert L.nlf_create(ctypes.byref(g), ctypes.byref(h)) == -9     # periodic: unsupported
+    assert L.nlf_create(ctypes.byref(g), ctypes.byref(h)) == -1     # only PEC and CPML axes exist

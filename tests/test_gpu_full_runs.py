@@ -1,0 +1,64 @@
+"""The configured workloads at full length on the GPU against the FP64
+oracle's stored run of the same problem (tests/golden/full_run_<name>.npz,
+written by tests/golden/make_full_run_golden.py, which calls only the
+oracle): the whole grid, material, source, monitors and number of time
+steps as configured.
+
+Bars (those of the field and spectrum parity tests): relative L2 of each
+vector field (E, H, P_f) over the stored sample sites <= 1e-4, and of each
+field's norm over the whole grid <= 1e-4; the raw DFT accumulators of the
+stored flux records and of the incident record <= 1e-4 relative to their
+largest magnitude; sigma_ext within 1e-3 of its largest magnitude where
+I >= 1e-3 max I (the spectrum's relative error, as in the parity tests); the
+extinction maximum at the same frequency (the 200 frequencies are 0.1 % or
+less apart)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2005_06997_gb300 import nlfdtd
+from paper_2005_06997_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+NAMES = ["sphere_ag_r2nm_48", "sphere_au_gnor_r10nm_224"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_full_length_run_matches_stored_oracle_run(name):
+    path = os.path.join(GOLDEN, "full_run_%s.npz" % name)
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle run for %s" % name)
+    g = np.load(path)
+    prob = W.CONFIGS[name]()
+    s = nlfdtd.Solver(prob)
+    s.run(prob["steps"])
+    s.sync()
+    assert s.n == prob["steps"]
+    errs = {}
+    for vec in ("E", "H", "P"):
+        num = den = n_got = n_ref = 0.0
+        for c in "xyz":
+            f = vec + c
+            a = s.field(f).astype(np.float64).reshape(-1)
+            ref = g["val_" + f]
+            num += float(np.sum((a[g["idx_" + f]] - ref) ** 2))
+            den += float(np.sum(ref ** 2))
+            n_got += float(np.sum(a * a))
+            n_ref += float(g["sumsq_" + f])
+        errs["samples_" + vec] = np.sqrt(num / den)
+        errs["norm_" + vec] = abs(np.sqrt(n_got) - np.sqrt(n_ref)) / np.sqrt(n_ref)
+    aE, aH = s.dft()
+    rows = g["rec_idx"]
+    for tag, got, ref in (("dftE", aE[rows], g["dftE"]), ("dftH", aH[rows], g["dftH"])):
+        errs[tag] = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    spec = s.spectra()
+    inc = g["inc"]
+    m = inc >= 1e-3 * inc.max()
+    errs["sigma_ext"] = float(np.max(np.abs(spec["ext"][m] - g["ext"][m])) / np.max(np.abs(g["ext"][m])))
+    bad = {k: v for k, v in errs.items() if not (v <= (1e-3 if k == "sigma_ext" else 1e-4))}
+    assert not bad, (bad, errs)
+    assert int(np.argmax(spec["ext"])) == int(np.argmax(g["ext"]))
+    s.close()
