@@ -44,7 +44,7 @@ extern "C" {
 #define NLF_OK             0
 #define NLF_E_ARG         (-1)  /* bad argument or inconsistent sizes */
 #define NLF_E_CFL         (-2)  /* S > 1/sqrt(3), or beta dt sqrt(3)/dx > 1 */
-#define NLF_E_GEOMETRY    (-3)  /* metal in the CPML / too close to the TF surface, bad boxes */
+#define NLF_E_GEOMETRY    (-3)  /* metal near a wall or the TF surface, bad boxes */
 #define NLF_E_OOM         (-4)  /* device allocation failed or bound buffer too small */
 #define NLF_E_CUDA        (-5)  /* a CUDA call failed */
 #define NLF_E_UNSTABLE    (-6)  /* a non-finite field was detected */
@@ -188,7 +188,15 @@ int nlf_set_materials(nlf_ctx* ctx, const nlf_material* mats, int n);
  * bit-exact): each E-site of Table Yee takes the material of the shape
  * containing its point, with no sub-cell averaging (the staircased surfaces
  * Sec. V discusses); P_f is carried only on those sites (the Pekar condition
- * of Sec. III).  Replaces any material map.  Errors: NLF_E_ARG. */
+ * of Sec. III).  Replaces any material map.  Errors: NLF_E_ARG.
+ *
+ * Geometry rules (checked at the first run, NLF_E_GEOMETRY): metal stays two
+ * cells clear of the outer walls.  With a TF/SF source it lies at least two
+ * cells inside the TF box (nonlocal metal only in the total-field region,
+ * Sec. III).  Without a source it may reach into a CPML slab (a substrate,
+ * say): the E-sites of CPML cells then follow the local Drude model, the
+ * material's beta and D taken as zero there, as Sec. III prescribes for a
+ * nonlocal structure that has to extend through the PML. */
 int nlf_set_shapes(nlf_ctx* ctx, const nlf_shape* shapes, int n);
 
 /* Alternative to shapes: a material id per E-site of Table Yee (0 =
@@ -275,6 +283,16 @@ int nlf_sync(nlf_ctx* ctx, int timeout_ms);
  * context's stream.  P outside the metal bounding box is zero.
  * Errors: NLF_E_ARG, NLF_E_STATE (no run yet), NLF_E_CUDA. */
 int nlf_get_field(nlf_ctx* ctx, int which, void* dst, int dst_on_device);
+
+/* Set E^n (NLF_FIELD_EX .. EZ, V/m) or H^{n-1/2} (NLF_FIELD_HX .. HZ, A/m) of
+ * the current time index from src, FP32 [nz][ny][nx], in device memory if
+ * src_on_device, else host: an initial field for a source-free problem (the
+ * first call allocates and initialises the state like nlf_run).  The
+ * polarisation histories keep their values: at time index 0 the problem then
+ * starts from rest with this field (E^{-1} = P^0 = P^{-1} = 0).  Tangential E
+ * on a PEC wall must be zero.  No counterpart in the paper.
+ * Errors: NLF_E_ARG, NLF_E_CUDA, and those of the first run's set-up. */
+int nlf_set_field(nlf_ctx* ctx, int which, const void* src, int src_on_device);
 
 /* Copy the voxelised material ids, uint8 [3][nz][ny][nx], to host dst (the
  * material of every E-site of Table Yee; 0 = background).  Errors: NLF_E_ARG,

@@ -440,6 +440,20 @@ void orc_graddiv(const orc_sim* s, const double* const* P, double* const* out)
 
 /* ------------------------------------------------- f2, f3, f4 (E, P_CP, P_f) */
 
+/* Is cell (i, j, k) inside a CPML slab (index < L or >= n - L along a CPML
+ * axis)?  Sec. III keeps the nonlocal response out of the PML: a nonlocal
+ * material that reaches into it (a substrate, say) is updated there with the
+ * local (LRA) Drude model, beta = D = 0. */
+static int in_cpml_cell(const orc_sim* s, int i, int j, int k)
+{
+    const int ix[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a) {
+        if (s->g.bc[a] != ORC_BC_CPML) continue;
+        if (ix[a] < s->g.pml || ix[a] >= axis_n(s, a) - s->g.pml) return 1;
+    }
+    return 0;
+}
+
 /* Tangential E on index 0 of a non-periodic axis is the PEC wall. */
 static int E_updated(const orc_sim* s, int c, int i, int j, int k)
 {
@@ -485,6 +499,12 @@ static void update_E_P(orc_sim* s)
                     size_t q = at(s, i, j, k);
                     uint8_t id = s->map[c][q];
                     coefs m = s->ctab[id];
+                    if (m.plasmonic && in_cpml_cell(s, i, j, k)) {
+                        /* local Drude inside the CPML (Sec. III): no pressure or diffusion term */
+                        m.DNL = 0.0;
+                        m.DG1 = 0.0;
+                        m.DG2 = 0.0;
+                    }
                     double En = s->E[c][q], Em = s->Eprev[c][q];
                     if (!E_updated(s, c, i, j, k)) {
                         s->Enew[c][q] = En;

@@ -60,27 +60,55 @@ __global__ void k_voxelise(const VoxParams v)
 // (component << 30) | box offset.  Each warp reserves its run with one atomic,
 // so runs land in any order while each run keeps box order; the material
 // update is independent per site, so the order does not change any result.
+// With g.only_pml the list keeps the sites of tiles that reach a CPML slab
+// (the EM kernel updates the others in its z-march); with g.tile_kr every
+// material site also widens the z range of its tile column.  count[0]
+// receives the entries, count[1] those with free electrons.
 __global__ void k_site_list(const uint8_t* __restrict__ mat, long long n3, uint32_t* sites, uint32_t* site_q,
                             long long nb, SiteGeom g, unsigned long long* count)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool has = t < n3 && mat[t] != 0;
-    const unsigned mask = __ballot_sync(0xffffffffu, has);
-    if (mask == 0u) return;
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint8_t id = t < n3 ? mat[t] : 0;
+    bool has = id != 0;
+    uint32_t c = 0, b = 0;
+    int i = 0, j = 0, k = 0;
     if (has) {
-        const uint32_t c = (uint32_t)(t / nb);
-        const uint32_t b = (uint32_t)(t - (long long)c * nb);
+        c = (uint32_t)(t / nb);
+        b = (uint32_t)(t - (long long)c * nb);
         const uint32_t bi = b % (uint32_t)g.bb_n[0], r = b / (uint32_t)g.bb_n[0];
         const uint32_t bj = r % (uint32_t)g.bb_n[1], bk = r / (uint32_t)g.bb_n[1];
+        i = g.bb_lo[0] + (int)bi;
+        j = g.bb_lo[1] + (int)bj;
+        k = g.bb_lo[2] + (int)bk;
+        if (g.tile_kr) {
+            int2* kr = g.tile_kr + (j / NLF_TILE_BY) * g.tiles_x + i / NLF_TILE_BX;
+            atomicMax(&kr->x, g.nz - k);
+            atomicMax(&kr->y, k + 1);
+        }
+        if (g.only_pml) {
+            const int n3g[3] = {g.nx, g.ny, g.nz};
+            has = cell_in_pml_tile(n3g, g.cpml, g.pml, g.kz, i, j, k);
+        }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, has);
+    if (mask == 0u) return;
+    const unsigned pmask = __ballot_sync(0xffffffffu, has && g.free_e[id]);
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) {
+        base = atomicAdd(&count[0], (unsigned long long)__popc(mask));
+        atomicAdd(&count[1], (unsigned long long)__popc(pmask));
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has) {
         const unsigned long long w = base + __popc(mask & ((1u << lane) - 1u));
-        sites[w] = (c << 30) | b;
-        site_q[w] = ((uint32_t)(g.bb_lo[2] + (int)bk) * (uint32_t)g.ny + (uint32_t)(g.bb_lo[1] + (int)bj)) *
-                        (uint32_t)g.px +
-                    (uint32_t)(g.bb_lo[0] + (int)bi);
+        // a site of a CPML cell is flagged: the metal is local Drude there
+        const int ix[3] = {i, j, k}, n3g[3] = {g.nx, g.ny, g.nz};
+        bool in_cpml = false;
+        for (int a = 0; a < 3; ++a)
+            if (g.cpml[a] && (ix[a] < g.pml || ix[a] >= n3g[a] - g.pml)) in_cpml = true;
+        sites[w] = (c << 30) | (in_cpml ? NLF_SITE_IN_CPML : 0u) | b;
+        site_q[w] = ((uint32_t)k * (uint32_t)g.ny + (uint32_t)j) * (uint32_t)g.px + (uint32_t)i;
     }
 }
 
@@ -89,6 +117,28 @@ void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, uint32_
 {
     const long long n = 3 * nb;
     k_site_list<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mat, n, sites, site_q, nb, g, count);
+}
+
+// Non-finite watchdog over the whole grid: every value of E^n (three
+// components, padding cells included, which stay zero).  A non-finite value
+// anywhere in the state reaches E within a step or two, so checking E once
+// per period covers the grid; it raises bit 0 of the error word.
+__global__ void __launch_bounds__(256) k_watch(const float4* __restrict__ E, long long n4, int* err)
+{
+    bool bad = false;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (long long)gridDim.x * blockDim.x) {
+        const float4 v = __ldg(E + q);
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, 1);
+}
+
+void launch_watch(const float* E, long long nfloats, int* err, cudaStream_t st)
+{
+    const long long n4 = nfloats / 4;
+    long long g = (n4 + 255) / 256;
+    if (g > 152LL * 8) g = 152LL * 8;
+    k_watch<<<(unsigned)g, 256, 0, st>>>(reinterpret_cast<const float4*>(E), n4, err);
 }
 
 void launch_voxelise(const VoxParams& v, cudaStream_t st)

@@ -28,6 +28,7 @@
 namespace nlf {
 void launch_step(const StepParams& p, cudaStream_t st);
 void launch_step_pml(const StepParams& p, cudaStream_t st);
+void launch_step_metal(const StepParams& p, cudaStream_t st);
 bool step_has_pml(const StepParams& p);
 long long tfsf_items(const StepParams& p);
 void launch_tfsf(const StepParams& p, cudaStream_t st);
@@ -45,6 +46,7 @@ void launch_flux(const double2* accE, const double2* accH, const double* coef, l
 void launch_plane_dft(const PlaneParams& m, const float* const* E, const float* const* P, const long long* step,
                       cudaStream_t st);
 void launch_field_out(const float* src, float* dst, int nx, int px, long long rows, float scale, cudaStream_t st);
+void launch_watch(const float* E, long long nfloats, int* err, cudaStream_t st);
 void launch_density_out(const DensityParams& d, float* dst, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st);
@@ -100,6 +102,12 @@ struct nlf_ctx {
     int bb_lo[3] = {0, 0, 0}, bb_n[3] = {0, 0, 0};
     long long nbb = 0;
     long long n_msites = 0;     // E-sites of the metal box that hold a material
+    // material update fused into the EM z-march (metal tiles): sites of CPML
+    // tiles stay on the site-list kernel (n_psites of them, n_ppl with free
+    // electrons); fuse is off with more than one critical-point pole
+    bool fuse = false;
+    int tiles_x = 0, tiles_y = 0;
+    long long n_psites = 0, n_ppl = 0;
     int inc_off = 0, inc_len = 0, inc_node = 0;
     int K = 1, B = 16, U = 128;
     long long nrec = 0, n_abs = 0;
@@ -118,7 +126,7 @@ struct nlf_ctx {
     size_t off_psiE[3] = {0, 0, 0}, off_psiH[2][3] = {{0, 0, 0}, {0, 0, 0}};
     size_t off_prof[3] = {0, 0, 0};
     size_t off_inc = 0;
-    size_t off_sites = 0, off_siteq = 0;
+    size_t off_sites = 0, off_siteq = 0, off_psites = 0, off_psiteq = 0, off_tilekr = 0;
     size_t off_mat = 0, off_P[2] = {0, 0}, off_auxf = 0, off_gdp = 0, off_pcp = 0, off_auxcp = 0, off_coef = 0,
            off_free = 0, off_counts = 0;
     size_t off_rec = 0, off_dcoef = 0, off_omega = 0, off_samples = 0, off_sstep = 0, off_phase = 0, off_acc = 0,
@@ -354,16 +362,20 @@ int plan(nlf_ctx* c)
     }
     c->has_metal = any;
     if (any) {
+        // the metal box (material extent and two cells around it) must lie in
+        // the grid: metal stays two cells clear of the outer walls.  It may
+        // reach into a CPML slab, where it follows the local Drude model
+        // (Sec. III); with a TF/SF source it must lie inside the TF box
+        // (check_boxes), which keeps it out of the CPML.
         for (int a = 0; a < 3; ++a) {
             c->bb_lo[a] = lo[a] - 2;
             c->bb_n[a] = hi[a] - lo[a] + 5;
-            int pl = c->g.boundary[a] == NLF_BC_CPML ? c->g.pml_cells : 0;
-            if (c->bb_lo[a] < pl + 1 || c->bb_lo[a] + c->bb_n[a] > n3[a] - pl - 1)
-                return fail(c, NLF_E_GEOMETRY, "metal reaches the CPML or the wall on axis %d", a);
+            if (c->bb_lo[a] < 0 || c->bb_lo[a] + c->bb_n[a] > n3[a])
+                return fail(c, NLF_E_GEOMETRY, "metal closer than two cells to the wall on axis %d", a);
         }
         c->nbb = (long long)c->bb_n[0] * c->bb_n[1] * c->bb_n[2];
-        if (c->nbb >= (1LL << 30))
-            return fail(c, NLF_E_GEOMETRY, "metal bounding box of %lld cells exceeds 2^30", c->nbb);
+        if (c->nbb > (long long)NLF_SITE_OFFSET_MASK)
+            return fail(c, NLF_E_GEOMETRY, "metal bounding box of %lld cells exceeds 2^29", c->nbb);
     }
     if (c->have_src) {
         int rc = check_boxes(c);
@@ -424,12 +436,29 @@ int plan(nlf_ctx* c)
     if (c->have_src) c->off_inc = take(10 * (size_t)c->inc_len * sizeof(float));
     c->off_coef = take((NLF_MAX_MAT + 1) * sizeof(nlf::MatCoef));
     c->off_free = take((NLF_MAX_MAT + 1) * sizeof(int));
-    c->off_counts = take(4 * sizeof(unsigned long long));
+    c->off_counts = take(8 * sizeof(unsigned long long));
+    c->tiles_x = (c->g.nx + NLF_TILE_BX - 1) / NLF_TILE_BX;
+    c->tiles_y = (c->g.ny + NLF_TILE_BY - 1) / NLF_TILE_BY;
+#ifdef NLF_NO_FUSE
+    c->fuse = false;                  // build option: every material site on the site-list kernel
+#else
+    // fused when the metal box is a quarter of the grid or more: a smaller
+    // particle gives the metal kernel too few tiles to fill the GPU, and the
+    // site-list kernel is then faster (224^3 sphere, 10 % of the cells in its
+    // box: 0.185 against 0.204 ms per step; 512^3 cube, 25 %: 2.10 against
+    // 1.91); contexts with more than one critical-point pole are not fused
+    c->fuse = c->has_metal && c->max_poles <= 1 && 4 * c->nbb >= c->ncell;
+#endif
     if (c->has_metal) {
         const size_t nb = (size_t)c->nbb;
         c->off_mat = take(3 * nb);
         c->off_sites = take(3 * nb * sizeof(uint32_t));
         c->off_siteq = take(3 * nb * sizeof(uint32_t));
+        if (c->fuse) {
+            c->off_psites = take(3 * nb * sizeof(uint32_t));
+            c->off_psiteq = take(3 * nb * sizeof(uint32_t));
+            c->off_tilekr = take((size_t)c->tiles_x * c->tiles_y * sizeof(int2));
+        }
         c->off_P[0] = take(3 * nb * sizeof(float));
         c->off_P[1] = take(3 * nb * sizeof(float));
         c->off_auxf = take(3 * nb * sizeof(float));
@@ -464,6 +493,17 @@ int plan(nlf_ctx* c)
     return NLF_OK;
 }
 
+// L2 promotion of the tensor-map loads (build option NLF_TMA_L2_PROMO = 0,
+// 64, 128 or 256 bytes).
+#ifndef NLF_TMA_L2_PROMO
+#define NLF_TMA_L2_PROMO 128
+#endif
+constexpr CUtensorMapL2promotion kTmaPromotion =
+    NLF_TMA_L2_PROMO == 0 ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+    : NLF_TMA_L2_PROMO == 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+    : NLF_TMA_L2_PROMO == 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                              : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+
 // Tensor maps of the four field arrays for the TMA-fed step kernel: 4D
 // [3][nz][ny][px] floats, globally nx x ny x nz x 3 (cells past nx, below 0
 // or past the grid read as zero), boxes of NLF_TMA_BOX_X x (EY | HY) x 1 x 3.
@@ -490,8 +530,8 @@ int encode_maps(nlf_ctx* c)
         const cuuint32_t box[4] = {NLF_TMA_BOX_X, (cuuint32_t)(isE ? NLF_TMA_BOX_EY : NLF_TMA_BOX_HY), 1, 3};
         void* base = c->base + (isE ? c->off_E[m & 1] : c->off_H[m & 1]);
         CUresult r = encode(&c->tmaps[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, elem,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, kTmaPromotion,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(c, NLF_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
     return NLF_OK;
@@ -572,10 +612,19 @@ void fill_params(nlf_ctx* c)
                 p.bb_lo[a] = c->bb_lo[a];
                 p.bb_n[a] = c->bb_n[a];
             }
+            p.fuse_metal = c->fuse;
+            p.tiles_x = c->tiles_x;
+            if (c->fuse) {
+                p.tile_kr = at<int2>(c, c->off_tilekr);
+                p.psites = at<uint32_t>(c, c->off_psites);
+                p.psite_q = at<uint32_t>(c, c->off_psiteq);
+            }
+            // the site list the post-step kernel walks: the CPML tiles' sites
+            // when the z march updates the others, else every material site
+            p.sites = at<uint32_t>(c, c->fuse ? c->off_psites : c->off_sites);
+            p.site_q = at<uint32_t>(c, c->fuse ? c->off_psiteq : c->off_siteq);
             for (int k = 0; k < 3; ++k) {
                 p.mat[k] = at<uint8_t>(c, c->off_mat) + k * nb;
-                p.sites = at<uint32_t>(c, c->off_sites);
-                p.site_q = at<uint32_t>(c, c->off_siteq);
                 p.P0[k] = at<float>(c, c->off_P[r]) + k * nb;
                 p.P1[k] = at<float>(c, c->off_P[w]) + k * nb;
                 p.auxf[k] = at<float>(c, c->off_auxf) + k * nb;
@@ -752,18 +801,43 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         for (int a = 0; a < 3; ++a) {
             sg.bb_lo[a] = c->bb_lo[a];
             sg.bb_n[a] = c->bb_n[a];
+            sg.cpml[a] = c->g.boundary[a] == NLF_BC_CPML;
         }
+        sg.nx = c->g.nx;
         sg.ny = c->g.ny;
+        sg.nz = c->g.nz;
         sg.px = c->px;
+        sg.pml = c->g.pml_cells;
+        sg.tiles_x = c->tiles_x;
+        sg.free_e = at<int>(c, c->off_free);
+        // every material site (the batched update walks this list), and the
+        // z range of material sites per tile column
+        sg.tile_kr = c->fuse ? at<int2>(c, c->off_tilekr) : nullptr;
         nlf::launch_site_list(at<uint8_t>(c, c->off_mat), c->nbb, at<uint32_t>(c, c->off_sites),
                               at<uint32_t>(c, c->off_siteq), sg,
                               at<unsigned long long>(c, c->off_counts) + 3, st);
         CK(cudaGetLastError());
         c->launches += 1;
+        if (c->fuse) {
+            // the sites of CPML tiles, for the post-step kernel (the tiling
+            // of the single-grid step)
+            nlf::StepParams tmp{};
+            tmp.nx = c->g.nx;
+            tmp.ny = c->g.ny;
+            tmp.nz = c->g.nz;
+            sg.tile_kr = nullptr;
+            sg.only_pml = 1;
+            sg.kz = nlf::step_kz(tmp);
+            nlf::launch_site_list(at<uint8_t>(c, c->off_mat), c->nbb, at<uint32_t>(c, c->off_psites),
+                                  at<uint32_t>(c, c->off_psiteq), sg,
+                                  at<unsigned long long>(c, c->off_counts) + 5, st);
+            CK(cudaGetLastError());
+            c->launches += 1;
+        }
     }
     fill_params(c);
     // info
-    unsigned long long cnts[4] = {0, 0, 0, 0};
+    unsigned long long cnts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(cnts, c->base + c->off_counts, sizeof cnts, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->d2h += (long long)sizeof cnts;
@@ -771,6 +845,8 @@ int initialise(nlf_ctx* c, cudaStream_t st)
     in.cells = c->ncell;
     in.metal_sites = (long long)(cnts[0] + cnts[1] + cnts[2]);
     c->n_msites = (long long)cnts[3];
+    c->n_psites = c->fuse ? (long long)cnts[5] : c->n_msites;
+    c->n_ppl = c->fuse ? (long long)cnts[6] : in.metal_sites;
     in.pole_sites = c->max_poles > 0 ? in.metal_sites : 0;
     in.bbox_cells = c->nbb;
     in.pml_slab_cells = c->pml_slab[0] + c->pml_slab[1] + c->pml_slab[2];
@@ -779,9 +855,17 @@ int initialise(nlf_ctx* c, cudaStream_t st)
     in.gnor = c->any_gnor;
     in.n_poles = c->max_poles;
     in.material_sites = c->n_msites;
-    in.step_kernel_bytes = 48.0 * c->ncell + 32.0 * in.pml_slab_cells;
-    in.metal_kernel_bytes = 21.0 * c->n_msites + 8.0 * (2 + (c->any_gnor ? 1 : 0)) * in.metal_sites +
-                            16.0 * c->max_poles * in.pole_sites;
+    // the EM kernels: E and H once, CPML psi, and the material update of the
+    // sites they update in their march (material id, P_f, a_f, the GNOR
+    // history, P_CP and a_CP read and written); the post-step kernel: the
+    // site-list update of the CPML tiles' sites (entry and cell offset, id,
+    // E read and written, H, and the same hydrodynamic state)
+    const double hydro = 8.0 * (2 + (c->any_gnor ? 1 : 0));
+    const double pole = 16.0 * c->max_poles;
+    const long long f_sites = c->n_msites - c->n_psites, f_pl = in.metal_sites - c->n_ppl;
+    in.step_kernel_bytes = 48.0 * c->ncell + 32.0 * in.pml_slab_cells + 1.0 * f_sites + hydro * f_pl +
+                           (c->max_poles ? pole * f_pl : 0.0);
+    in.metal_kernel_bytes = 21.0 * c->n_psites + hydro * c->n_ppl + (c->max_poles ? pole * c->n_ppl : 0.0);
     in.step_bytes = in.step_kernel_bytes + in.metal_kernel_bytes;
     c->ready = true;
     return NLF_OK;
@@ -817,7 +901,8 @@ void monitor_work(nlf_ctx* c, cudaStream_t st);
 void launch_em(nlf_ctx* c, cudaStream_t st)
 {
     const nlf::StepParams& sp = c->sp[c->n & 1];
-    if (nlf::step_has_pml(sp)) {
+    const bool pml = nlf::step_has_pml(sp);
+    if (pml) {
         cudaEventRecord(c->fork, st);
         cudaStreamWaitEvent(c->aux, c->fork, 0);
         nlf::launch_step_pml(sp, c->aux);
@@ -829,6 +914,13 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
         nlf::launch_step(sp, st);
         c->launches += 1;
     }
+    // the metal tiles after the others, alone on the GPU (run beside them,
+    // the three kernels' streams contend for L2 and the step takes longer
+    // than the three in sequence: 2.05 against 1.92 ms on the 512^3 cube)
+    if (c->fuse && c->n_msites > c->n_psites) {
+        nlf::launch_step_metal(sp, st);
+        c->launches += 1;
+    }
 }
 
 // The work after the EM step of time step n: the TF/SF corrections and the
@@ -837,26 +929,32 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
 void launch_post(nlf_ctx* c, cudaStream_t st)
 {
     const nlf::StepParams& sp = c->sp[c->n & 1];
-    const bool tf = nlf::tfsf_items(sp) > 0, met = c->n_msites > 0;
+    const bool tf = nlf::tfsf_items(sp) > 0, met = c->n_psites > 0;
     if (tf && met) {
-        nlf::launch_post(sp, c->n_msites, st);
+        nlf::launch_post(sp, c->n_psites, st);
         c->launches += 1;
     } else if (tf) {
         nlf::launch_tfsf(sp, st);
         c->launches += 1;
     } else if (met) {
-        nlf::launch_metal(sp, c->n_msites, st);
+        nlf::launch_metal(sp, c->n_psites, st);
         c->launches += 1;
     }
 }
 
-// One time step and its monitor work, launched on st.
+// One time step and its monitor work, launched on st; at the end of every
+// period (U steps, one captured graph) the whole-grid non-finite watchdog.
 void step_once(nlf_ctx* c, cudaStream_t st)
 {
     launch_em(c, st);
     launch_post(c, st);
     c->n += 1;
     monitor_work(c, st);
+    if (c->n % c->U == 0) {
+        const int cur = (int)(c->n & 1);
+        nlf::launch_watch(at<float>(c, c->off_E[cur]), 3 * c->nfield, &at<Header>(c, c->off_hdr)->err, st);
+        c->launches += 1;
+    }
 }
 
 // The running-DFT work due after time step n (c->n already advanced).
@@ -979,6 +1077,12 @@ int plan_descriptors(BatchPlan* P, int kz)
         nlf_ctx* x = P->ctxs[q];
         params[2 * q] = x->sp[0];
         params[2 * q + 1] = x->sp[1];
+        for (int g2 = 0; g2 < 2 && x->has_metal; ++g2) {
+            // batched steps update every material site from the full list
+            params[2 * q + g2].fuse_metal = 0;
+            params[2 * q + g2].sites = at<uint32_t>(x, x->off_sites);
+            params[2 * q + g2].site_q = at<uint32_t>(x, x->off_siteq);
+        }
         nlf::BatchInst& b = inst[q];
         b.tiles_x = (x->g.nx + 31) / 32;
         b.tiles_y = (x->g.ny + 7) / 8;
@@ -1087,6 +1191,15 @@ long long plan_launch(BatchPlan* P, cudaStream_t st)
         if (P->met_sites > 0) {
             nlf::launch_metal_batch(bs, P->met_sites, st);
             ++nodes;
+        }
+        if (s + 1 == P->U) {
+            // the whole-grid non-finite watchdog of every instance
+            for (size_t q = 0; q < P->ctxs.size(); ++q) {
+                nlf_ctx* x = P->ctxs[q];
+                const int cur = (P->par[q] + P->U) & 1;
+                nlf::launch_watch(at<float>(x, x->off_E[cur]), 3 * x->nfield, &at<Header>(x, x->off_hdr)->err, st);
+                ++nodes;
+            }
         }
         if (P->mon && (s + 1) % P->K == 0) {
             nlf::BatchDft bd = P->bd;
@@ -1600,6 +1713,37 @@ int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
                         (float)(kEps0 * sub[((size_t)bk * c->bb_n[1] + bj) * c->bb_n[0] + bi]);
     }
     CK(cudaMemcpy(dst, full.data(), n * sizeof(float), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return NLF_OK;
+}
+
+int nlf_set_field(nlf_ctx* c, int which, const void* src, int src_on_device)
+{
+    if (!c || !src || which < NLF_FIELD_EX || which > NLF_FIELD_HZ) return NLF_E_ARG;
+    int rc = ensure_ready(c, c->stream);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    CK(cudaStreamSynchronize(st));
+    const int cur = (int)(c->n & 1);
+    const int comp = which % 3;
+    float* dst = at<float>(c, which < 3 ? c->off_E[cur] : c->off_H[cur]) + comp * (size_t)c->nfield;
+    const long long rows = (long long)c->g.ny * c->g.nz;
+    const size_t n = (size_t)c->ncell;
+    // into the padded rows; H is held as eta0 H
+    std::vector<float> h;
+    const float* from = static_cast<const float*>(src);
+    if (src_on_device) {
+        h.resize(n);
+        CK(cudaMemcpy(h.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
+        from = h.data();
+    }
+    if (which >= 3) {
+        if (h.empty()) h.assign(from, from + n);
+        for (size_t q = 0; q < n; ++q) h[q] = (float)(h[q] * c->eta0);
+        from = h.data();
+    }
+    CK(cudaMemcpy2D(dst, (size_t)c->px * sizeof(float), from, (size_t)c->g.nx * sizeof(float),
+                    (size_t)c->g.nx * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice));
+    c->h2d += (long long)(n * sizeof(float));
     return NLF_OK;
 }
 

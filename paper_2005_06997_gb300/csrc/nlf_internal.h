@@ -24,12 +24,43 @@
 #define NLF_TMA_BOX_EY 10
 #define NLF_TMA_BOX_HY 9
 #define NLF_MAX_SHP 16
+// Material site list entries: component << 30 | flag | box offset
+#define NLF_SITE_IN_CPML (1u << 29)          // the site's cell lies in a CPML slab
+#define NLF_SITE_OFFSET_MASK ((1u << 29) - 1u)
+// Tiles of the EM z-march: BX x BY columns of cells, marched along z in
+// chunks of kz planes
+#define NLF_TILE_BX 32
+#define NLF_TILE_BY 8
 #define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
 #define NLF_INC_MARGIN 10       // vacuum cells between the TF box and that CPML
 #define NLF_MAX_BATCH 256       // instances in one batched launch
 #define NLF_BATCH_RCH 32        // records per block of the batched accumulation
 
 namespace nlf {
+
+// The CPML slab axes that the cell box [lo, hi] (inclusive) reaches, bit a
+// for axis a (0: clear of every slab).
+__host__ __device__ __forceinline__ int pml_axes_of_box(const int n3[3], const int cpml[3], int pml, const int lo[3],
+                                                         const int hi[3])
+{
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (cpml[a] && (lo[a] < pml || hi[a] >= n3[a] - pml)) m |= 1 << a;
+    return m;
+}
+
+// Does the tile holding cell (i, j, k) reach a CPML slab (its one-cell halo
+// included)?  Tiles are NLF_TILE_BX x NLF_TILE_BY x kz.
+__host__ __device__ __forceinline__ bool cell_in_pml_tile(const int n3[3], const int cpml[3], int pml, int kz, int i,
+                                                          int j, int k)
+{
+    const int x0 = i / NLF_TILE_BX * NLF_TILE_BX, y0 = j / NLF_TILE_BY * NLF_TILE_BY, k0 = k / kz * kz;
+    const int k1 = k0 + kz < n3[2] ? k0 + kz : n3[2];
+    const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
+    const int hi[3] = {x0 + NLF_TILE_BX, y0 + NLF_TILE_BY, k1};
+    return pml_axes_of_box(n3, cpml, pml, lo, hi) != 0;
+}
 
 // Per-material FP32 coefficients of the increment form of f2/f3/f4.
 struct MatCoef {
@@ -103,7 +134,7 @@ struct StepParams {
     int has_metal;
     int bb_lo[3], bb_n[3];
     const uint8_t* mat[3];
-    const uint32_t* sites;      // material E-sites of the box: (component << 30) | box offset
+    const uint32_t* sites;      // material E-sites of the box: (component << 30) | CPML flag | box offset
     const uint32_t* site_q;     // their cell offsets in the field arrays
     const MatCoef* coef;        // [n_materials + 1], index 0 unused
     const float* P0[3];
@@ -114,6 +145,15 @@ struct StepParams {
     float* auxcp[NLF_MAX_POLES][3];
     int any_gnor;
     int max_poles;
+    // material update fused into the EM z-march: tile column (bx, by) holds
+    // material E-sites on cell planes [nz - tile_kr.x, tile_kr.y - 1] (both 0:
+    // none); its tiles run k_step_metal.  Sites of CPML tiles keep the
+    // site-list update (psites, n_psites entries).
+    int fuse_metal;
+    int tiles_x;
+    const int2* tile_kr;
+    const uint32_t* psites;
+    const uint32_t* psite_q;
 
     // step counters: step0 holds n, block 0 writes n+1 into step1
     const long long* step0;
@@ -154,10 +194,20 @@ struct DensityParams {
     double eps0_dx;             // eps0 / dx
 };
 
-// Where the metal box sits in the field arrays (for the site list).
+// Where the metal box sits in the field arrays (for the site list), and the
+// tiling that decides which sites the fused EM kernel updates: with
+// only_pml set, the list keeps only the sites whose tile (BX x BY x kz, its
+// one-cell halo included) reaches a CPML slab; tile_kr receives the z range
+// of material sites of every tile column.
 struct SiteGeom {
     int bb_lo[3], bb_n[3];
-    int ny, px;
+    int nx, ny, nz, px;
+    int only_pml;
+    int kz, pml;
+    int cpml[3];
+    int tiles_x;
+    int2* tile_kr;
+    const int* free_e;          // [NLF_MAX_MAT + 1]
 };
 
 struct DftParams {

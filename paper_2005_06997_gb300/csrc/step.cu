@@ -51,7 +51,7 @@
 
 namespace nlf {
 
-constexpr int BX = 32, BY = 8;
+constexpr int BX = NLF_TILE_BX, BY = NLF_TILE_BY;
 static_assert(NLF_TMA_BOX_X == BX + 8 && NLF_TMA_BOX_EY == BY + 2 && NLF_TMA_BOX_HY == BY + 1,
               "tensor-map boxes must match the tile");
 
@@ -196,14 +196,60 @@ __device__ __forceinline__ float node_div(const StepParams& p, uint32_t b, uint3
            (__ldg(p.P0[2] + b) - __ldg(p.P0[2] + b - sz));
 }
 
-// Material update of E-site (C, box offset b) after the EM step: E^{n+1}
+// The material update of E-site (C, box offset b) of material id: E^{n+1}
 // from Eq. discreteamperes with f3 and f4 substituted (increment form), then
-// P_CP^{n+1} and P_f^{n+1}.  The curl uses H^{n+1/2} just written by the step
-// (material sites lie at least two cells inside the TF box and outside the
-// CPML, so neither correction applies there).  Every operand is loaded before
-// the material's coefficients are consulted, so one memory round trip serves
-// the whole site; arrays a material does not use are read and ignored.
-template <int C>
+// P_CP^{n+1} and P_f^{n+1}.  curl = the plain difference curl of H^{n+1/2} at
+// the site, gd_raw = the difference of the node divergences of P_f^n,
+// p_old, af_raw, g1, pc, ac the site's P_f^n, a_f^n, GD^{n-1}, P_CP^n and
+// a_CP^n (arrays a material does not use are read and ignored: gd_raw and
+// af_raw for a material without free electrons, poles past its own count).
+// Returns E^{n+1}; writes the site's hydrodynamic and pole state.
+template <int C, int NPMAX>
+__device__ __forceinline__ float site_update(const StepParams& p, uint32_t b, int id, float En, float curl,
+                                             float gd_raw, float p_old, float af_raw, float g1, float (&pc)[NPMAX],
+                                             float (&ac)[NPMAX], bool local = false)
+{
+    const MatCoef& m = p.coef[id];
+    // local: a site of a CPML cell, where the metal follows the local Drude
+    // model (no pressure or diffusion term: G = D_G2 = 0), Sec. III
+    const float mG = local ? 0.f : m.G, mDG2 = local ? 0.f : m.DG2;
+    const float gd = m.free_e ? gd_raw : 0.f;
+    const float af = m.free_e ? af_raw : 0.f;
+    float acs = 0.f;
+#pragma unroll
+    for (int pp = 0; pp < NPMAX; ++pp) {
+        if (pp >= m.npoles) ac[pp] = 0.f;
+        acs += ac[pp];
+    }
+    const float delta = (p.S * curl - af - acs - mG * gd - m.cE * En) * m.inv_den;
+    if (m.free_e) {
+        const float dP = af + m.D3 * (3.f * En + delta) + mG * gd;
+        p.P1[C][b] = p_old + dP;
+        float a_new = fmaf(-m.g2, dP, dP) + m.D3 * En;      // -D2 dP + D3 E^n
+        if (m.gnor) {
+            a_new += mDG2 * (g1 - 4.f * gd);
+            p.gdp[C][b] = gd;
+        }
+        p.auxf[C][b] = a_new;
+    }
+#pragma unroll
+    for (int pp = 0; pp < NPMAX; ++pp) {
+        if (pp >= m.npoles) break;
+        const float dPc = ac[pp] + m.C3[pp] * (En + delta) + m.C4[pp] * En;
+        const float pcn = pc[pp] + dPc;
+        p.pcp[pp][C][b] = pcn;
+        p.auxcp[pp][C][b] = -m.kap[pp] * pcn + fmaf(-m.c2g[pp], dPc, dPc) + m.C5[pp] * En;
+    }
+    return En + delta;
+}
+
+// Material update of E-site (C, box offset b) after the EM step, from the
+// site list (sites of tiles that the fused z-march does not update): the
+// curl uses H^{n+1/2} just written by the step (material sites lie at least
+// two cells inside the TF box and outside the CPML, so neither correction
+// applies there).  Every operand is loaded before the material's
+// coefficients are consulted, so one memory round trip serves the whole site.
+template <int C, bool PMLS = false>
 __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint32_t q)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
@@ -224,43 +270,36 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
         ac[pp] = pp < p.max_poles ? p.auxcp[pp][C][b] : 0.f;
         pc[pp] = pp < p.max_poles ? p.pcp[pp][C][b] : 0.f;
     }
-    const MatCoef& m = p.coef[id];
-    const float curl = (h2 - h2m) - (h1 - h1m);
-    const float gd = m.free_e ? gd_raw : 0.f;
-    const float af = m.free_e ? af_raw : 0.f;
-    float acs = 0.f;
-#pragma unroll
-    for (int pp = 0; pp < NLF_MAX_POLES; ++pp) {
-        if (pp >= m.npoles) ac[pp] = 0.f;
-        acs += ac[pp];
+    float t1 = h2 - h2m, t2 = h1 - h1m;
+    if constexpr (PMLS) {
+        // a site of a CPML cell: the step kernel has already advanced the
+        // site's psi_E of each derivative whose slab holds the cell; the
+        // curl takes them as the background update does
+        const uint32_t bi = b % (uint32_t)p.bb_n[0], r = b / (uint32_t)p.bb_n[0];
+        const uint32_t bj = r % (uint32_t)p.bb_n[1], bk = r / (uint32_t)p.bb_n[1];
+        Cell c = make_cell(p, p.bb_lo[0] + (int)bi, p.bb_lo[1] + (int)bj, p.bb_lo[2] + (int)bk, true);
+        if (c.l[A1] >= 0) t1 += p.psiE[A1][1][c.s[A1]];
+        if (c.l[A2] >= 0) t2 += p.psiE[A2][0][c.s[A2]];
     }
-    const float delta = (p.S * curl - af - acs - m.G * gd - m.cE * En) * m.inv_den;
-    p.E1[C][q] = En + delta;
-    if (m.free_e) {
-        const float dP = af + m.D3 * (3.f * En + delta) + m.G * gd;
-        p.P1[C][b] = p_old + dP;
-        float a_new = fmaf(-m.g2, dP, dP) + m.D3 * En;      // -D2 dP + D3 E^n
-        if (m.gnor) {
-            a_new += m.DG2 * (g1 - 4.f * gd);
-            p.gdp[C][b] = gd;
-        }
-        p.auxf[C][b] = a_new;
-    }
-#pragma unroll
-    for (int pp = 0; pp < NLF_MAX_POLES; ++pp) {
-        if (pp >= m.npoles) break;
-        const float dPc = ac[pp] + m.C3[pp] * (En + delta) + m.C4[pp] * En;
-        const float pcn = pc[pp] + dPc;
-        p.pcp[pp][C][b] = pcn;
-        p.auxcp[pp][C][b] = -m.kap[pp] * pcn + fmaf(-m.c2g[pp], dPc, dPc) + m.C5[pp] * En;
-    }
+    const float curl = t1 - t2;
+    p.E1[C][q] = site_update<C, NLF_MAX_POLES>(p, b, id, En, curl, gd_raw, p_old, af_raw, g1, pc, ac, PMLS);
 }
 
-// Entry t of the material site list (box entry e, cell offset q).
+// Entry t of the material site list (box entry e: component << 30, bit 29
+// set for a site of a CPML cell, box offset below; cell offset q).
 __device__ __forceinline__ void metal_entry(const StepParams& p, long long t)
 {
     const uint32_t e = __ldg(p.sites + t), q = __ldg(p.site_q + t);
-    const uint32_t c = e >> 30, b = e & 0x3fffffffu;
+    const uint32_t c = e >> 30, b = e & NLF_SITE_OFFSET_MASK;
+    if (e & NLF_SITE_IN_CPML) {
+        if (c == 0)
+            metal_site<0, true>(p, b, q);
+        else if (c == 1)
+            metal_site<1, true>(p, b, q);
+        else
+            metal_site<2, true>(p, b, q);
+        return;
+    }
     if (c == 0)
         metal_site<0>(p, b, q);
     else if (c == 1)
@@ -507,19 +546,38 @@ constexpr int TMA_E_STAGE = (TMA_E_FLOATS * 4 + 127) / 128 * 32;   // floats, 12
 constexpr int TMA_H_STAGE = (TMA_H_FLOATS * 4 + 127) / 128 * 32;
 constexpr int NE_STAGE = 4, NH_STAGE = 3;      // background tiles
 constexpr int NE_PML = 3, NH_PML = 2, PML_BLOCKS = 4;   // CPML tiles (also stage psi): 4 blocks per SM
+#ifdef NLF_TEST_TMA_STALL
+// test-only build: the first E stage of every k_step block expects more
+// bytes than its copy delivers, so its (shortened) bounded wait runs out
+constexpr long long TMA_SPIN = 1LL << 10;
+constexpr unsigned TMA_TEST_EXTRA = 16;
+#else
 constexpr long long TMA_SPIN = 1LL << 21;      // bounded mbarrier wait (~2 s at the hint below)
+constexpr unsigned TMA_TEST_EXTRA = 0;
+#endif
 
 struct NoPsi {};
 
-template <int NE, int NH, bool PML>
+// Metal tiles: node divergences of P_f^n (difference units) on three planes,
+// plane q in slot q mod 3 (at plane k the z march reads planes k and k+1 and
+// writes k+1; with one block barrier per plane a slot is rewritten only after
+// every thread has left the last plane that read it), for the tile's own
+// nodes and one node past it along +x and +y.
+struct MetShared {
+    float d[3][BY + 1][BX + 1];
+};
+
+template <int NE, int NH, bool PML, bool MET = false>
 struct TileSharedTMA {
     static constexpr int kNE = NE, kNH = NH;
+    static constexpr bool kPoisonFree = PML || MET;     // only the background kernel's tiles in the stall test
     alignas(128) float sE[NE][TMA_E_STAGE];
     alignas(128) float sHo[NH][TMA_H_STAGE];
     float sH[2][3][BY + 1][BX + 1];
     unsigned long long barE[NE];
     unsigned long long barH[NH];
     typename std::conditional<PML, PsiShared, NoPsi>::type ps;
+    typename std::conditional<MET, MetShared, NoPsi>::type met;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
@@ -587,7 +645,10 @@ struct TmaRing {
     __device__ void issue_e(int pl)
     {
         const int q = eslot(pl);
-        tma_plane(sm.sE[q], p.tmE, x0 - 4, y0 - 1, pl, &sm.barE[q], TMA_E_FLOATS * 4);
+        // (TMA_TEST_EXTRA: 0 except in the stall test build, which poisons
+        // the first E stage of the background kernel's blocks)
+        const unsigned extra = (TMA_TEST_EXTRA && !SM::kPoisonFree && pl == k0 - 1) ? TMA_TEST_EXTRA : 0u;
+        tma_plane(sm.sE[q], p.tmE, x0 - 4, y0 - 1, pl, &sm.barE[q], TMA_E_FLOATS * 4 + extra);
         pendE |= 1u << q;
         parE = (parE & ~(1u << q)) | (epar(pl) << q);
     }
@@ -635,12 +696,75 @@ __device__ __forceinline__ void cpml_pair(const PsiShared& ps, int w, int ux, in
     pr2 = cpml_coef<(C + 2) % 3>(ps, w, ux, uy, z);
 }
 
+// ------------------------------------------------- fused material update
+//
+// Metal tiles update their material E-sites inside the z march: E^{n+1} from
+// Eq. discreteamperes with f3 and f4 substituted, P_CP and P_f (site_update),
+// with GD^n = grad(div P_f^n) as the difference of node divergences staged in
+// shared memory (MetShared).
+
+// Material ids of the three E-sites of cell (i, j, k) (one byte each), 0
+// outside the metal box; bi, bj are the cell's box-local column.
+__device__ __forceinline__ uint32_t site_ids(const StepParams& p, bool in, int bi, int bj, int k)
+{
+    const int bk = k - p.bb_lo[2];
+    if (!in || bi < 0 || bj < 0 || bk < 0 || bi >= p.bb_n[0] || bj >= p.bb_n[1] || bk >= p.bb_n[2]) return 0u;
+    const uint32_t b = ((uint32_t)bk * (uint32_t)p.bb_n[1] + (uint32_t)bj) * (uint32_t)p.bb_n[0] + (uint32_t)bi;
+    return (uint32_t)__ldg(p.mat[0] + b) | ((uint32_t)__ldg(p.mat[1] + b) << 8) |
+           ((uint32_t)__ldg(p.mat[2] + b) << 16);
+}
+
+// The six P_f^n values of the node divergence at node (i, j, k): P_x at the
+// node and one cell down x, P_y likewise along y, P_z along z; zero unless
+// the node lies at least one cell inside the metal box (no material site
+// reads the divergence anywhere else).
+__device__ __forceinline__ void div_load(const StepParams& p, int i, int j, int k, float (&v)[6])
+{
+    const int bi = i - p.bb_lo[0], bj = j - p.bb_lo[1], bk = k - p.bb_lo[2];
+    if (bi < 1 || bj < 1 || bk < 1 || bi >= p.bb_n[0] || bj >= p.bb_n[1] || bk >= p.bb_n[2]) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = 0.f;
+        return;
+    }
+    const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
+    const uint32_t b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
+    v[0] = __ldg(p.P0[0] + b);
+    v[1] = __ldg(p.P0[0] + b - 1);
+    v[2] = __ldg(p.P0[1] + b);
+    v[3] = __ldg(p.P0[1] + b - sy);
+    v[4] = __ldg(p.P0[2] + b);
+    v[5] = __ldg(p.P0[2] + b - sz);
+}
+
+// The divergence from the six values, in the order of node_div.
+__device__ __forceinline__ float div_sum(const float (&v)[6]) { return (v[0] - v[1]) + (v[2] - v[3]) + (v[4] - v[5]); }
+
+// Node (x, y) of the tile's divergence plane that thread tid fills besides
+// its own: the node past the tile along +x (tid < BY) or +y (BY <= tid <
+// BY + BX); false for the other threads.
+__device__ __forceinline__ bool div_extra(int tid, int& x, int& y)
+{
+    if (tid < BY) {
+        x = BX;
+        y = tid;
+        return true;
+    }
+    if (tid < BY + BX) {
+        x = tid - BY;
+        y = BY;
+        return true;
+    }
+    return false;
+}
+
 // The z march of one tile over planes [k0, k1).  PML (uniform per block):
 // the tile or its halo reaches a CPML slab (psi arithmetic, psi staged by
-// cp.async).
-template <bool PML, int AX, class SM>
+// cp.async).  MP >= 0: a metal tile whose material sites (with at most MP
+// critical-point poles) are updated in the march.
+template <bool PML, int AX, class SM, int MP = -1>
 __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, int k0, int k1, SM& sm)
 {
+    constexpr bool MET = MP >= 0;
     constexpr int NE = SM::kNE, NH = SM::kNH;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = x0 + tx, j = y0 + ty;
@@ -699,10 +823,68 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     if constexpr (PML) psi_plane<AX>(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid);
     bool fail = __syncthreads_or(r.bad);
     if (!fail && tid == 0 && k0 + NE - 1 <= k1) r.issue_e(k0 + NE - 1);
+    // metal tile: the planes of this chunk that hold material sites of the
+    // tile column, the own cell's box column, and the material ids of the
+    // next plane (loaded a plane ahead)
+    int kmin = 1, kmax = 0, mbi = 0, mbj = 0;
+    uint32_t idn = 0;
+    bool prev_mp = false;
+    if constexpr (MET) {
+        const int2 kr = p.tile_kr[(y0 / BY) * p.tiles_x + x0 / BX];
+        kmin = max(p.nz - kr.x, k0);
+        kmax = min(kr.y - 1, k1 - 1);
+        mbi = i - p.bb_lo[0];
+        mbj = j - p.bb_lo[1];
+        if (kmin == k0 && kmin <= kmax) idn = site_ids(p, in, mbi, mbj, k0);
+    }
     int hb = 0, pb = 0;
     for (int k = k0; k < k1 && !fail; ++k) {
         float (*sH)[BY + 1][BX + 1] = sm.sH[hb];
         const bool more = k + 1 < k1;
+        // metal plane: operands of the material sites and of the node
+        // divergences of plane k+1, issued before the plane's H work so that
+        // their latency overlaps it
+        const bool mp = MET && k >= kmin && k <= kmax;
+        uint32_t ids = 0, bsite = 0;
+        float so_p[3] = {}, so_a[3] = {}, so_g[3] = {}, so_c[3][1] = {}, so_q[3][1] = {};
+        float dv_own[6] = {}, dv_ext[6] = {};
+        int ex_x = 0, ex_y = 0;
+        bool has_ext = false;
+        if constexpr (MET) {
+            if (mp) {
+                has_ext = div_extra(tid, ex_x, ex_y);
+                if (!prev_mp) {
+                    // entering the metal: divergences of plane k itself
+                    float v[6];
+                    div_load(p, i, j, k, v);
+                    sm.met.d[k % 3][ty][tx] = div_sum(v);
+                    if (has_ext) {
+                        div_load(p, x0 + ex_x, y0 + ex_y, k, v);
+                        sm.met.d[k % 3][ex_y][ex_x] = div_sum(v);
+                    }
+                }
+                div_load(p, i, j, k + 1, dv_own);
+                if (has_ext) div_load(p, x0 + ex_x, y0 + ex_y, k + 1, dv_ext);
+                ids = idn;
+                if (ids) {
+                    const int bk = k - p.bb_lo[2];
+                    bsite = ((uint32_t)bk * (uint32_t)p.bb_n[1] + (uint32_t)mbj) * (uint32_t)p.bb_n[0] + (uint32_t)mbi;
+#pragma unroll
+                    for (int C = 0; C < 3; ++C) {
+                        if (!((ids >> (8 * C)) & 0xffu)) continue;
+                        so_p[C] = __ldg(p.P0[C] + bsite);
+                        so_a[C] = p.auxf[C][bsite];
+                        so_g[C] = p.any_gnor ? p.gdp[C][bsite] : 0.f;
+                        if constexpr (MP >= 1) {
+                            so_c[C][0] = p.pcp[0][C][bsite];
+                            so_q[C][0] = p.auxcp[0][C][bsite];
+                        }
+                    }
+                }
+            }
+            idn = (k + 1 >= kmin && k + 1 <= kmax) ? site_ids(p, in, mbi, mbj, k + 1) : 0u;
+            prev_mp = mp;
+        }
         r.wait_e(k + 1);
         r.wait_h(k);
         // this plane's stages: E^n of planes k and k+1, H^{n-1/2} of plane k
@@ -797,6 +979,12 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                 }
             }
         }
+        if constexpr (MET) {
+            if (mp) {
+                sm.met.d[(k + 1) % 3][ty][tx] = div_sum(dv_own);
+                if (has_ext) sm.met.d[(k + 1) % 3][ex_y][ex_x] = div_sum(dv_ext);
+            }
+        }
         fail = __syncthreads_or(r.bad);
         if (fail) break;
         // E plane k and H plane k have had their last reader: refill their stages
@@ -833,9 +1021,33 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                 else
                     p.E1[2][c.q] = 0.f;
             } else {
-                p.E1[0][c.q] = (j >= 1 && k >= 1) ? ex + p.Sb * ((hz - hzm) - (hy - hy_prev)) : 0.f;
-                p.E1[1][c.q] = (i >= 1 && k >= 1) ? ey + p.Sb * ((hx - hx_prev) - (hz - hzi)) : 0.f;
-                p.E1[2][c.q] = (i >= 1 && j >= 1) ? ez + p.Sb * ((hy - hyi) - (hx - hxm)) : 0.f;
+                const float cx = (hz - hzm) - (hy - hy_prev);
+                const float cy = (hx - hx_prev) - (hz - hzi);
+                const float cz = (hy - hyi) - (hx - hxm);
+                float nx = (j >= 1 && k >= 1) ? ex + p.Sb * cx : 0.f;
+                float ny = (i >= 1 && k >= 1) ? ey + p.Sb * cy : 0.f;
+                float nz = (i >= 1 && j >= 1) ? ez + p.Sb * cz : 0.f;
+                if constexpr (MET) {
+                    if (ids) {
+                        // material sites (never on a wall): GD from the staged divergences
+                        const float (*dk)[BX + 1] = sm.met.d[k % 3];
+                        const float (*dk1)[BX + 1] = sm.met.d[(k + 1) % 3];
+                        const float d0 = dk[ty][tx];
+                        const uint32_t idx = ids & 0xffu, idy = (ids >> 8) & 0xffu, idz = (ids >> 16) & 0xffu;
+                        if (idx)
+                            nx = site_update<0, 1>(p, bsite, idx, ex, cx, dk[ty][tx + 1] - d0, so_p[0], so_a[0],
+                                                   so_g[0], so_c[0], so_q[0]);
+                        if (idy)
+                            ny = site_update<1, 1>(p, bsite, idy, ey, cy, dk[ty + 1][tx] - d0, so_p[1], so_a[1],
+                                                   so_g[1], so_c[1], so_q[1]);
+                        if (idz)
+                            nz = site_update<2, 1>(p, bsite, idz, ez, cz, dk1[ty][tx] - d0, so_p[2], so_a[2],
+                                                   so_g[2], so_c[2], so_q[2]);
+                    }
+                }
+                p.E1[0][c.q] = nx;
+                p.E1[1][c.q] = ny;
+                p.E1[2][c.q] = nz;
             }
         }
         hx_prev = hx;
@@ -854,30 +1066,58 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
 // axis a (0: a background tile).
 __device__ __forceinline__ int tile_pml_axes(const StepParams& p, const int lo[3], const int hi[3])
 {
+    // the parameter block's members are copied, not addressed (an address
+    // would move the block to local memory)
     const int n3[3] = {p.nx, p.ny, p.nz};
-    int m = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        if (p.cpml[a] && (lo[a] < p.pml || hi[a] >= n3[a] - p.pml)) m |= 1 << a;
-    return m;
+    const int cp[3] = {p.cpml[0], p.cpml[1], p.cpml[2]};
+    return pml_axes_of_box(n3, cp, p.pml, lo, hi);
 }
 
 
-// The single-grid step runs as two kernels over the same grid of tiles,
-// launched concurrently on two streams: k_step_pml takes the CPML tiles,
-// k_step the others, each block leaving at once if
-// its tile belongs to the other kernel.  Without CPML tiles k_step alone runs.
-// Separate kernels let the background tiles run TMA-fed with fewer
-// registers and without the psi staging area: 5 blocks per SM instead of 4.
-template <bool PMLK, class SM>
-__device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm)
+// The single-grid step runs as up to three kernels over the same grid of
+// tiles: k_step_pml takes the CPML tiles, k_step_metal the tiles that hold
+// material sites (with the material update fused), k_step the others, each
+// block leaving at once if its tile belongs to another kernel.  k_step and
+// k_step_pml run concurrently on two streams, k_step_metal after them.
+// Without CPML or metal tiles k_step alone runs.
+// Separate kernels let the background tiles run TMA-fed with fewer registers
+// and without the psi staging area or the divergence ring: 5 blocks per SM.
+enum { TILE_BG = 0, TILE_PML = 1, TILE_MET = 2 };
+
+// Does tile (bx, by) with chunk [k0, k1) hold material sites that the fused
+// march updates?
+__device__ __forceinline__ bool metal_tile(const StepParams& p, int bx, int by, int k0, int k1)
+{
+    if (!p.fuse_metal) return false;
+    const int2 kr = p.tile_kr[by * p.tiles_x + bx];
+    return p.nz - kr.x < k1 && kr.y - 1 >= k0;
+}
+
+// The metal kernel marches the planes that k_step leaves to it (the chunks of
+// kz planes that hold material sites of the tile column) in sub-chunks of
+// kzm planes (kzm divides kz): more, shorter marches for its heavier planes.
+// Returns false if sub-chunk bzm of tile (bx, by) is not one of them.
+__device__ __forceinline__ bool metal_subchunk(const StepParams& p, int bx, int by, int bzm, int kz, int kzm, int& k0,
+                                               int& k1)
+{
+    k0 = bzm * kzm;
+    k1 = min(k0 + kzm, p.nz);
+    const int c0 = k0 / kz * kz, c1 = min(c0 + kz, p.nz);     // the k_step chunk holding it
+    return metal_tile(p, bx, by, c0, c1);
+}
+
+template <int KIND, int MP, class SM>
+__device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm, int kzm = 0)
 {
     const int x0 = bx * BX, y0 = by * BY;
-    const int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    if constexpr (KIND == TILE_MET) {
+        if (!metal_subchunk(p, bx, by, bz, kz, kzm, k0, k1)) return;
+    }
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
     const int ax = tile_pml_axes(p, lo, hi);
-    if constexpr (PMLK) {
+    if constexpr (KIND == TILE_PML) {
         // tiles touching one slab axis run code with that axis' psi only
         if (ax == 1)
             march_tma<true, 1>(p, x0, y0, k0, k1, sm);
@@ -887,11 +1127,17 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
             march_tma<true, 4>(p, x0, y0, k0, k1, sm);
         else if (ax != 0)
             march_tma<true, 7>(p, x0, y0, k0, k1, sm);
+    } else if constexpr (KIND == TILE_MET) {
+        // the chunk's PML class is that of k_step's chunk, which holds the sub-chunk
+        const int c0 = k0 / kz * kz, c1 = min(c0 + kz, p.nz);
+        const int clo[3] = {x0 - 1, y0 - 1, c0 - 1};
+        const int chi[3] = {x0 + BX, y0 + BY, c1};
+        if (tile_pml_axes(p, clo, chi) == 0) march_tma<false, 0, SM, MP>(p, x0, y0, k0, k1, sm);
     } else {
-        if (ax == 0) march_tma<false, 0>(p, x0, y0, k0, k1, sm);
+        if (ax == 0 && !metal_tile(p, bx, by, k0, k1)) march_tma<false, 0>(p, x0, y0, k0, k1, sm);
     }
     // the 1D incident grid and the step counter: block (0,0,0) of k_step
-    if (!PMLK && bx == 0 && by == 0 && bz == 0) {
+    if (KIND == TILE_BG && bx == 0 && by == 0 && bz == 0) {
         const int tid = threadIdx.y * BX + threadIdx.x;
         if (p.tfsf) inc_step(p, tid, BX * BY);
         if (tid == 0) *p.step1 = *p.step0 + 1;
@@ -900,14 +1146,32 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
 
 using SharedBG = TileSharedTMA<NE_STAGE, NH_STAGE, false>;
 using SharedPML = TileSharedTMA<NE_PML, NH_PML, true>;
+using SharedMET = TileSharedTMA<NE_STAGE, NH_STAGE, false, true>;
 // PML_BLOCKS blocks of the CPML kernel (plus the 1 KB the SM reserves per
 // block) must fit the SM's 228 KB of shared memory
 static_assert(PML_BLOCKS * (sizeof(SharedPML) + 128 + 1024) <= 228 * 1024, "CPML tile blocks do not fit an SM");
+static_assert(sizeof(SharedMET) <= 48 * 1024, "metal tile shared memory exceeds the static limit");
 
 __global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
 {
     __shared__ SharedBG sm;
-    step_tile_of<false>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
+    step_tile_of<TILE_BG, -1>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
+}
+
+// Metal tiles, MP critical-point poles at most.  Resident blocks per SM
+// (4: 64 registers per thread) and the sub-chunk of the metal march
+// (kz / NLF_METAL_KZ_DIV planes, at least 4) are build-time choices.
+#ifndef NLF_METAL_BLOCKS
+#define NLF_METAL_BLOCKS 4
+#endif
+#ifndef NLF_METAL_KZ_DIV
+#define NLF_METAL_KZ_DIV 2
+#endif
+template <int MP>
+__global__ void __launch_bounds__(BX * BY, NLF_METAL_BLOCKS) k_step_metal(const StepParams p, int kz, int kzm)
+{
+    __shared__ SharedMET sm;
+    step_tile_of<TILE_MET, MP>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm, kzm);
 }
 
 // CPML tiles: TMA rings plus the psi staging area exceed the 48 KB of static
@@ -922,7 +1186,7 @@ __global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_pml(const StepPara
     // few CPML tiles of middle chunks, which share the SMs with background
     // tiles instead of running as an under-filled tail
     const int zb = (int)blockIdx.z, nzb = (int)gridDim.z;
-    step_tile_of<true>(p, blockIdx.x, blockIdx.y, (zb & 1) ? nzb - 1 - (zb >> 1) : (zb >> 1), kz, sm);
+    step_tile_of<TILE_PML, -1>(p, blockIdx.x, blockIdx.y, (zb & 1) ? nzb - 1 - (zb >> 1) : (zb >> 1), kz, sm);
 }
 
 // ---------------------------------------------------------------- batched
@@ -1126,7 +1390,7 @@ __device__ __forceinline__ void batch_item(const BatchStep& a, SM& sm, StepParam
     const long long rem = r - bz * per_plane;
     const int by = (int)(rem / I.tiles_x);
     const int bx = (int)(rem - (long long)by * I.tiles_x);
-    step_tile_of<PMLK>(sp, bx, by, bz, I.kz, sm);
+    step_tile_of<PMLK ? TILE_PML : TILE_BG, -1>(sp, bx, by, bz, I.kz, sm);
 }
 
 __global__ void __launch_bounds__(BX * BY, 5) k_step_batch(const BatchStep a)
@@ -1242,6 +1506,18 @@ void launch_step(const StepParams& p, cudaStream_t st)
     dim3 blk(BX, BY, 1);
     dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
     k_step<<<grd, blk, 0, st>>>(p, kz);
+}
+
+void launch_step_metal(const StepParams& p, cudaStream_t st)
+{
+    const int kz = step_kz(p);
+    const int kzm = max(min(4, kz), kz / NLF_METAL_KZ_DIV);
+    dim3 blk(BX, BY, 1);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kzm - 1) / kzm);
+    if (p.max_poles >= 1)
+        k_step_metal<1><<<grd, blk, 0, st>>>(p, kz, kzm);
+    else
+        k_step_metal<0><<<grd, blk, 0, st>>>(p, kz, kzm);
 }
 
 void launch_step_pml(const StepParams& p, cudaStream_t st)

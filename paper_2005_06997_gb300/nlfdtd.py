@@ -89,6 +89,7 @@ SIGNATURES = {
     "nlf_reset": (C.c_int, [_P, C.c_void_p]),
     "nlf_sync": (C.c_int, [_P, C.c_int]),
     "nlf_get_field": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_int]),
+    "nlf_set_field": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_int]),
     "nlf_get_voxels": (C.c_int, [_P, C.c_void_p]),
     "nlf_get_spectra": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nlf_get_dft": (C.c_int, [_P, C.c_void_p]),
@@ -318,6 +319,12 @@ class Solver:
         out = np.empty(self.shape3, dtype=np.float32)
         _check(self.h, self.L.nlf_get_field(self.h, FIELD[name], out.ctypes.data, 0))
         return out
+
+    def set_field(self, name: str, values):
+        """Set E^n or H^{n-1/2} ("Ex".."Hz", SI) from a [nz][ny][nx] array."""
+        a = np.ascontiguousarray(values, dtype=np.float32)
+        assert a.shape == self.shape3
+        _check(self.h, self.L.nlf_set_field(self.h, FIELD[name], a.ctypes.data, 0))
 
     def field_to_device(self, name: str, dst_ptr: int):
         _check(self.h, self.L.nlf_get_field(self.h, FIELD[name], C.c_void_p(dst_ptr), 1))

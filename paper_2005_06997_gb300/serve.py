@@ -1,13 +1,23 @@
 """Continuous-batching solve server over the C ABI (torch for memory and streams).
 
 Requests (problem dicts with an ``arrival_s`` time) arrive on a clock.  The
-server admits waiting requests first in, first out, while their state fits
-the HBM budget and the batch has a free slot: each admitted request gets a
-torch device buffer bound with ``nlf_bind_state`` and its state stays on the
-device until it finishes.  All admitted requests advance together, one DFT
-period (K * B time steps) per ``nlf_batch_run`` call, so requests that arrive
-while others are running join at the next period boundary; finished requests
-are retired there, their spectra copied out and their memory returned.
+server admits every arrived request whose state fits the HBM budget: it gets
+a torch device buffer bound with ``nlf_bind_state`` and its state stays on
+the device until it finishes.  Admission runs on a stream of its own while
+the GPU works on the current period.
+
+Scheduling, one DFT period (K * B time steps) at a time: the admitted
+requests are taken in order of remaining work (cells x remaining steps,
+smallest first) until their grids fill the GPU (``fill_cells``); those
+advance together in one ``nlf_batch_run`` call (a single grid runs alone
+through ``nlf_run``, the single-grid kernels).  Small grids, which leave
+most of the GPU idle on their own, share periods; a large grid runs alone,
+so small requests are not held to its step rate.  A request that has not
+advanced for ``max_wait_s`` joins the next period whatever its size, so
+large requests are not starved.  Requests that arrive while others run join
+at the next period boundary; finished requests are retired there, their
+spectra copied out and their memory returned.  ``cancel`` drops a waiting
+request or retires an admitted one at the next boundary.
 
 ``serve_fifo`` is the plain form for comparison: one request at a time, in
 arrival order, one grid per launch sequence.
@@ -21,9 +31,11 @@ import numpy as np
 
 from . import nlfdtd
 
+CANCELLED = -100          # status of a cancelled request
+
 
 class _Active:
-    __slots__ = ("req", "solver", "buf", "remaining", "admit_s")
+    __slots__ = ("req", "solver", "buf", "remaining", "admit_s", "last_run_s", "cells", "cancelled")
 
     def __init__(self, req, solver, buf, admit_s):
         self.req = req
@@ -31,6 +43,12 @@ class _Active:
         self.buf = buf
         self.remaining = int(req["steps"])
         self.admit_s = admit_s
+        self.last_run_s = admit_s
+        self.cells = float(np.prod(req["shape"]))
+        self.cancelled = False
+
+    def work(self):
+        return self.cells * self.remaining
 
 
 def _percentile(v, q):
@@ -38,23 +56,52 @@ def _percentile(v, q):
 
 
 def summarise(results, wall_s):
-    lat = [r["latency_s"] for r in results]
-    work = sum(r["cell_updates"] for r in results)
-    return {"solves": len(results), "wall_s": wall_s, "solves_per_s": len(results) / wall_s if wall_s > 0 else None,
+    done = [r for r in results if r["status"] == 0]
+    lat = [r["latency_s"] for r in done]
+    work = sum(r["cell_updates"] for r in done)
+    return {"solves": len(done), "wall_s": wall_s, "solves_per_s": len(done) / wall_s if wall_s > 0 else None,
             "p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
             "gcell_updates_per_s": work / wall_s / 1e9 if wall_s > 0 else None}
 
 
+def plan_period(active, now, fill_cells, max_wait_s):
+    """The requests that advance in the next period: those waiting longer
+    than max_wait_s first, then the others by remaining work, smallest
+    first, while the grids' cells stay within fill_cells (at least one
+    request always runs).  A request larger than fill_cells runs alone
+    unless an overdue request joins it.  Host logic only."""
+    overdue = [a for a in active if now - a.last_run_s > max_wait_s]
+    rest = sorted((a for a in active if now - a.last_run_s <= max_wait_s), key=lambda a: a.work())
+    run = list(overdue)
+    cells = sum(a.cells for a in run)
+    for a in rest:
+        if run and cells + a.cells > fill_cells:
+            continue
+        run.append(a)
+        cells += a.cells
+    return run
+
+
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, stream=None):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 256, stream=None, fill_cells: float = 16e6,
+                 max_wait_s: float = 1.0):
         import torch
         nlfdtd.require_gpu()
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
         self.max_active = int(max_active)
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.init_stream = torch.cuda.Stream()
+        self.fill_cells = float(fill_cells)
+        self.max_wait_s = float(max_wait_s)
         self.used = 0
         self.launches = 0
+        self._cancel = set()
+
+    def cancel(self, name):
+        """Cancel the request called `name`: dropped if still waiting, retired
+        at the next period boundary if admitted (status CANCELLED)."""
+        self._cancel.add(name)
 
     def _admit(self, req, now):
         s = nlfdtd.Solver(req, block_b=SERVE_B)
@@ -62,87 +109,115 @@ class Server:
         buf = self.torch.empty(nb + 256, dtype=self.torch.uint8, device="cuda")
         ptr = (buf.data_ptr() + 255) // 256 * 256
         s.bind_state(ptr, nb)
-        s.reset(self.stream.cuda_stream)
+        s.reset(self.init_stream.cuda_stream)
         self.used += nb
         return _Active(req, s, buf, now)
 
-    def _admit_waiting(self, waiting, active, sizes, now):
-        """Admit waiting requests, first in first out, by HBM budget and slots."""
+    def _admit_waiting(self, waiting, active, sizes, now, results):
+        """Admit waiting requests in arrival order by HBM budget and slots; a
+        request larger than the whole budget is refused (NLF_E_OOM)."""
         while waiting and len(active) < self.max_active:
             req = waiting[0]
+            if req.get("name") in self._cancel:
+                waiting.popleft()
+                results.append(_result(req, None, now, CANCELLED))
+                continue
             key = id(req)
             if key not in sizes:
                 probe = nlfdtd.Solver(req, block_b=SERVE_B)
                 sizes[key] = probe.state_bytes()
                 probe.close()
-            if self.used + sizes[key] > self.budget and active:
+            if sizes[key] > self.budget:
+                waiting.popleft()
+                results.append(_result(req, None, now, -4))
+                continue
+            if self.used + sizes[key] > self.budget:
                 break
             waiting.popleft()
             active.append(self._admit(req, now))
 
     def run(self, requests, clock=time.perf_counter):
-        """Serve `requests` (sorted by arrival_s); returns (results, summary).
-
-        Each loop iteration enqueues one DFT period of the running batch, then
-        admits the requests that arrived meanwhile on the host while the GPU
-        works (their initialisation is queued behind the period on the same
-        stream), then waits and retires the finished requests."""
+        """Serve `requests` (sorted by arrival_s); returns (results, summary)."""
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival_s"]))
         waiting = collections.deque()
         active = []
         results = []
         t0 = clock()
         sizes = {}
+        torch = self.torch
         while pending or waiting or active:
             now = clock() - t0
             while pending and pending[0]["arrival_s"] <= now:
                 waiting.append(pending.popleft())
+            self._admit_waiting(waiting, active, sizes, now, results)
             if not active:
-                self._admit_waiting(waiting, active, sizes, now)
-                if not active:
-                    if pending:
-                        time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
-                    continue
+                if pending:
+                    time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
+                continue
             U = _period(active[0])
-            steps = [min(U, a.remaining) for a in active]
-            running = list(active)
-            before = sum(a.solver.launches for a in running)
-            status = nlfdtd.batch_run([a.solver for a in running], steps, self.stream.cuda_stream)
+            run = plan_period(active, now, self.fill_cells, self.max_wait_s)
+            steps = [min(U, a.remaining) for a in run]
+            before = sum(a.solver.launches for a in run)
+            if len(run) == 1:
+                run[0].solver.run(steps[0], self.stream.cuda_stream)
+                status = [0]
+            else:
+                status = nlfdtd.batch_run([a.solver for a in run], steps, self.stream.cuda_stream)
+            done_ev = torch.cuda.Event()
+            done_ev.record(self.stream)
             # host work while the GPU runs the period: admit new arrivals
-            now = clock() - t0
-            while pending and pending[0]["arrival_s"] <= now:
-                waiting.append(pending.popleft())
-            self._admit_waiting(waiting, active, sizes, now)
-            self.stream.synchronize()
-            self.launches += sum(a.solver.launches for a in running) - before
+            while not done_ev.query():
+                now = clock() - t0
+                while pending and pending[0]["arrival_s"] <= now:
+                    waiting.append(pending.popleft())
+                if waiting:
+                    self._admit_waiting(waiting, active, sizes, now, results)
+                else:
+                    time.sleep(0.0002)
+            self.launches += sum(a.solver.launches for a in run) - before
             now = clock() - t0
             done = set()
-            for a, n, st in zip(running, steps, status):
+            for a, n, st in zip(run, steps, status):
                 a.remaining -= n
-                if st != 0 or a.remaining <= 0:
-                    res = {"name": a.req.get("name"), "arrival_s": a.req["arrival_s"], "admit_s": a.admit_s,
-                           "finish_s": now, "latency_s": now - a.req["arrival_s"], "status": int(st),
-                           "cell_updates": float(np.prod(a.req["shape"])) * int(a.req["steps"])}
-                    if st == 0:
+                a.last_run_s = now
+            for a, st in zip(run, status):
+                cancelled = a.req.get("name") in self._cancel
+                if st != 0 or a.remaining <= 0 or cancelled:
+                    code = CANCELLED if cancelled and st == 0 and a.remaining > 0 else int(st)
+                    res = _result(a.req, a.admit_s, now, code)
+                    if code == 0:
                         res["spectra"] = a.solver.spectra()
                     results.append(res)
+                    done.add(id(a))
+            # cancelled requests that did not run this period
+            for a in active:
+                if id(a) not in done and a.req.get("name") in self._cancel:
+                    results.append(_result(a.req, a.admit_s, now, CANCELLED))
+                    done.add(id(a))
+            for a in active:
+                if id(a) in done:
                     self.used -= a.solver.state_bytes()
                     a.solver.close()
                     a.buf = None
-                    done.add(id(a))
             active = [a for a in active if id(a) not in done]
         wall = clock() - t0
         return results, summarise(results, wall)
 
 
-# Samples buffered per DFT flush for served requests: a batched segment is one
-# DFT period (K * SERVE_B steps), so this sets how often finished requests
-# leave and new ones join.
+def _result(req, admit_s, now, status):
+    return {"name": req.get("name"), "arrival_s": req["arrival_s"], "admit_s": admit_s, "finish_s": now,
+            "latency_s": now - req["arrival_s"], "status": int(status),
+            "cell_updates": float(np.prod(req["shape"])) * int(req["steps"])}
+
+
+# Samples buffered per DFT flush for served requests: a period is one DFT
+# period (K * SERVE_B steps), so this sets how often finished requests leave
+# and new ones join.
 SERVE_B = 16
 
 
 def _period(a):
-    """Time steps of one DFT period of an active request (the batching unit)."""
+    """Time steps of one DFT period of an active request (the scheduling unit)."""
     mon = a.req.get("monitors")
     K = mon.get("K", 16) if mon else 1
     kb = K * SERVE_B
@@ -168,9 +243,9 @@ def serve_fifo(requests, stream=None, clock=time.perf_counter):
         launches += s.launches
         s.close()
         fin = clock() - t0
-        results.append({"name": req.get("name"), "arrival_s": req["arrival_s"], "admit_s": start, "finish_s": fin,
-                        "latency_s": fin - req["arrival_s"], "status": 0, "spectra": spec,
-                        "cell_updates": float(np.prod(req["shape"])) * int(req["steps"])})
+        r = _result(req, start, fin, 0)
+        r["spectra"] = spec
+        results.append(r)
     wall = clock() - t0
     out = summarise(results, wall)
     out["launches"] = launches

@@ -443,3 +443,50 @@ def test_full_size_au_gnor_224_grid():
     g, o = run_pair(prob, steps)
     errs = assert_fields_match(g, o)
     assert np.max(np.abs(o.array("Px"))) > 0
+
+
+# ------------------------------------------------- fused material update
+
+def mixed_tile_problem(material=None, steps=0):
+    """An 80^3 grid whose sphere (radius 23 cells, centred; its metal box
+    holds more than a quarter of the cells, so the material update is fused
+    into the EM march) spans the x tiles [0, 32) and [64, 80), which reach
+    the 6-cell CPML, and [32, 64), which does not: the sites of the first are
+    updated by the site-list kernel, those of the second inside the EM
+    z-march of the metal tiles."""
+    mat = material if material is not None else W.AU_LIKE_GNOR
+    prob = W.small_sphere(n=80, radius_cells=23.0, pml=6, material=mat, steps=steps, nf=8, K=4,
+                          center_offset_half=(0, 0, 0))
+    return prob
+
+
+def test_fields_fused_and_site_list_material_updates():
+    prob = mixed_tile_problem()
+    g, o = run_pair(prob, 800)
+    assert np.max(np.abs(o.array("Px"))) > 0
+    assert_fields_match(g, o)
+    aEg, aHg = g.dft()
+    aEo, aHo = o.dft()
+    assert rel_l2(aEg, aEo) < 1e-4
+    assert rel_l2(aHg, aHo) < 1e-4
+
+
+def test_fused_update_equals_site_list_update():
+    """The same problem once with one Lorentz pole (metal tiles update their
+    sites in the z march) and once with a second pole of zero strength
+    (A = 0: no contribution at all, but more than one pole keeps every site on
+    the site-list kernel): the two paths agree to FP32 rounding."""
+    one = mixed_tile_problem()
+    two = copy.deepcopy(one)
+    two["materials"][0]["poles"] = list(two["materials"][0]["poles"]) + [(0.0, W.ev(3.0), W.ev(0.3), 0.0)]
+    a = nlfdtd.Solver(one)
+    b = nlfdtd.Solver(two)
+    a.run(800)
+    b.run(800)
+    a.sync()
+    b.sync()
+    for f in FIELDS:
+        x, y = a.field(f), b.field(f)
+        assert rel_l2(x, y) <= 1e-6, f
+    a.close()
+    b.close()

@@ -86,3 +86,50 @@ def test_fifo_matches_batched():
     for r in res_f:
         assert_close(r["spectra"], fb[r["name"]]["spectra"])
     assert summ_f["solves"] == 3
+
+
+@pytest.mark.parametrize("when", ["waiting", "running"])
+def test_cancelled_request_leaves_the_others_unchanged(when):
+    """A request cancelled before it is admitted is dropped; one cancelled
+    while it runs (here: when the next request is admitted) is retired at
+    the next period boundary.  The others finish as they would alone."""
+    reqs = small_requests(5, spread_s=0.05)
+    victim = reqs[2]["name"]
+    srv = serve.Server(hbm_budget_bytes=64 << 30)
+    if when == "waiting":
+        srv.cancel(victim)
+    else:
+        orig = srv._admit
+
+        def admit(req, now):
+            a = orig(req, now)
+            if req["name"] == reqs[3]["name"]:
+                srv.cancel(victim)
+            return a
+
+        srv._admit = admit
+    results, summary = srv.run(reqs)
+    by_name = {r["name"]: r for r in results}
+    assert by_name[victim]["status"] == serve.CANCELLED
+    assert "spectra" not in by_name[victim]
+    assert summary["solves"] == len(reqs) - 1
+    for q in reqs:
+        if q["name"] != victim:
+            assert_close(by_name[q["name"]]["spectra"], alone_spectra(q))
+    assert srv.used == 0
+
+
+def test_request_larger_than_the_budget_is_refused():
+    reqs = small_requests(3)
+    sizes = []
+    for q in reqs:
+        s = nlfdtd.Solver(q, block_b=serve.SERVE_B)      # as the server sizes them
+        sizes.append(s.state_bytes())
+        s.close()
+    big = int(np.argmax(sizes))
+    srv = serve.Server(hbm_budget_bytes=max(sizes) - 1)
+    results, summary = srv.run(reqs)
+    by_name = {r["name"]: r for r in results}
+    assert by_name[reqs[big]["name"]]["status"] == -4        # NLF_E_OOM
+    assert summary["solves"] == len(reqs) - 1
+    assert srv.used == 0

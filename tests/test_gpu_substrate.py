@@ -1,0 +1,77 @@
+"""A nonlocal structure that extends through the PML (Sec. III: it follows
+the local Drude model inside the PML), on the GPU against the FP64 oracle.
+
+A GNOR slab runs along x through the CPML at both ends of a grid with a
+CPML on x and PEC walls on y and z, like a substrate; a smooth initial field
+(no source) excites it.  The GPU's CPML material sites take the CPML's psi
+terms in their curl and drop the pressure and diffusion terms."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_06997_gb300 import nlfdtd
+from paper_2005_06997_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VECTORS = {"E": ("Ex", "Ey", "Ez"), "H": ("Hx", "Hy", "Hz"), "P": ("Px", "Py", "Pz")}
+
+
+def slab_problem(beta=3.6e6, diff=1.9e-4, n=(32, 16, 16), pml=8):
+    mat = W.drude_material(9.0, 0.07, beta=beta, diff=diff, poles=[W.lorentz_pole()])
+    nx, ny, nz = n
+    sh = {"kind": "box", "material": 1, "c": (nx, ny, nz), "half": (nx - 5, 4, 4)}
+    return {"shape": n, "dx": 0.25e-9, "courant": 0.5, "pml": pml, "bc": ("cpml", "pec", "pec"), "eps_b": 1.0,
+            "materials": [mat], "shapes": [sh], "source": None, "monitors": None, "steps": 0}
+
+
+def blob(shape3):
+    nz, ny, nx = shape3
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    b = np.exp(-(((i - nx / 2) / 4.0) ** 2 + ((j - ny / 2 - 0.5) / 3.0) ** 2 + ((k - nz / 2) / 3.0) ** 2))
+    ey = np.zeros(shape3)
+    ex = np.zeros(shape3)
+    ey[1:, :, 1:] = b[1:, :, 1:]
+    ex[1:, 1:, :] = 0.5 * b[1:, 1:, :]
+    return ex, ey
+
+
+def start_pair(prob):
+    g = nlfdtd.Solver(prob)
+    o = oracle.Sim(prob)
+    ex, ey = blob(o.shape3)
+    o.array("Ex")[...] = ex
+    o.array("Ey")[...] = ey
+    g.set_field("Ex", ex)
+    g.set_field("Ey", ey)
+    return g, o
+
+
+def test_slab_through_the_cpml_matches_oracle():
+    prob = slab_problem()
+    g, o = start_pair(prob)
+    assert np.array_equal(g.field("Ey"), np.asarray(o.array("Ey"), dtype=np.float32))
+    g.run(600)
+    g.sync()
+    o.step(600)
+    for vec, comps in VECTORS.items():
+        num = sum(np.sum((g.field(c).astype(np.float64) - o.array(c)) ** 2) for c in comps)
+        den = sum(np.sum(np.asarray(o.array(c)) ** 2) for c in comps)
+        assert den > 0, vec
+        assert np.sqrt(num / den) <= 1e-4, (vec, np.sqrt(num / den))
+    # the slab's P_f is alive inside the CPML cells too
+    px = np.asarray(o.array("Px"))
+    assert np.max(np.abs(px[:, :, :8])) > 1e-3 * np.max(np.abs(px))
+    g.close()
+
+
+def test_slab_through_the_cpml_stays_bounded_on_the_gpu():
+    prob = slab_problem()
+    g, _ = start_pair(prob)
+    e2 = []
+    for _ in range(20):
+        g.run(500)
+        g.sync()
+        e2.append(sum(float(np.sum(g.field(c).astype(np.float64) ** 2)) for c in ("Ex", "Ey", "Ez")))
+    assert max(e2[-4:]) <= 1.5 * max(e2[:4]), e2
+    g.close()

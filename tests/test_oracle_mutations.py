@@ -91,6 +91,14 @@ MUTANTS = [
     ("flux: absorption taken as the outward (not inward) flux",
      "double sa = -sum[0] * dA / I, ss = sum[1] * dA / I;", "double sa = sum[0] * dA / I, ss = sum[1] * dA / I;",
      [FLUX]),
+    # the local Drude model inside the CPML (Sec. III)
+    ("nonlocal terms kept inside the CPML",
+     "if (m.plasmonic && in_cpml_cell(s, i, j, k)) {", "if (0 && m.plasmonic && in_cpml_cell(s, i, j, k)) {",
+     [P + "test_slab_through_the_cpml_stays_bounded"]),
+    ("local region of the CPML one cell short",
+     "if (ix[a] < s->g.pml || ix[a] >= axis_n(s, a) - s->g.pml) return 1;",
+     "if (ix[a] < s->g.pml - 1 || ix[a] >= axis_n(s, a) - s->g.pml) return 1;",
+     [P + "test_nonlocal_metal_in_the_cpml_is_local_drude_there"]),
     ("DFT: rectangle rule without the K dt factor",
      "double scale = s->mon.K * s->dt;", "double scale = s->dt;",
      [INC]),
