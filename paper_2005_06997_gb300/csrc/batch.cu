@@ -1,12 +1,13 @@
 // batch.cu -- many independent grids advanced together.
 //
-// A batch step is one persistent launch: a grid sized to the resident
-// capacity of the GPU walks a work list of (instance, tile, z chunk) items of
-// every active instance (heaviest instances first) and runs the same tile
-// code as the single-grid step.  The monitor work of all instances is batched
-// the same way (one gather launch per sample, one phase and one accumulation
-// launch per block of samples).  The host captures a whole DFT period of these
-// launches in a CUDA graph.
+// A batch step is one launch per kernel over the concatenated work of every
+// active instance: the step kernels take one block per (instance, tile, z
+// chunk) item of the joint work list (heaviest instances first) and run the
+// same tile code as the single-grid step; the material update walks the
+// joint material-site list grid-stride.  The monitor work of all instances is
+// batched the same way (one gather launch per sample, one phase and one
+// accumulation launch per block of samples).  The host captures a whole DFT
+// period of these launches in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,8 +79,9 @@ __global__ void k_phase_batch(const BatchDft a, int count)
     d.phase[t] = v;
 }
 
-// Same arithmetic as the single-grid accumulation: per record chunk and
-// frequency chunk, FP32 sums over the B samples added into FP64.
+// Same arithmetic as the single-grid accumulation: per group of
+// NLF_BATCH_GROUP record chunks and per frequency chunk, FP32 sums over the
+// B samples added into FP64; the phases a block stages serve the whole group.
 template <int B, int RCH>
 __global__ void __launch_bounds__(ACC_NT) k_accum_batch(const BatchDft a)
 {
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(ACC_NT) k_accum_batch(const BatchDft a)
     const DftParams& d = a.inst[q].d;
     const int f0 = blockIdx.y * ACC_NT;
     if (f0 >= d.nf) return;
-    accum_block<B, RCH>(d, (w - (q > 0 ? a.chunk_end[q - 1] : 0)) * RCH, 1, f0, sm);
+    accum_block<B, RCH>(d, (w - (q > 0 ? a.chunk_end[q - 1] : 0)) * RCH * NLF_BATCH_GROUP, NLF_BATCH_GROUP, f0, sm);
 }
 
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st)

@@ -34,7 +34,8 @@
 #define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
 #define NLF_INC_MARGIN 10       // vacuum cells between the TF box and that CPML
 #define NLF_MAX_BATCH 256       // instances in one batched launch
-#define NLF_BATCH_RCH 32        // records per block of the batched accumulation
+#define NLF_BATCH_RCH 32        // records per chunk of the batched accumulation
+#define NLF_BATCH_GROUP 8       // chunks per block of the batched accumulation
 
 namespace nlf {
 
@@ -259,7 +260,7 @@ struct BatchDft {
     const BatchDftInst* inst;   // [n]
     const long long* rec_end;   // [n] prefix sums of (records + 1)
     const long long* ph_end;    // [n] prefix sums of B * nf
-    const long long* chunk_end; // [n] prefix sums of record chunks
+    const long long* chunk_end; // [n] prefix sums of record groups (NLF_BATCH_GROUP chunks of NLF_BATCH_RCH)
     int n;
     int cur_par;                // generation parity of the fields just written
 };

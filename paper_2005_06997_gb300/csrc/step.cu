@@ -98,6 +98,7 @@ struct Cell {
     uint32_t q;
     int l[3];
     uint32_t s[3];
+    int wm = 7;         // bit a: some lane of the warp has its cell in the slab of axis a (else its psi work is skipped)
 };
 
 __device__ __forceinline__ void cell_slabs(const StepParams& p, Cell& c)
@@ -145,12 +146,12 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
         // pr = (b, c) of the derivative's axis at the cell; selects, not
         // branches: lanes in and out of a slab take one path
         // AX: the slab axes the tile touches (compile time); others have no psi here
-        if (AX >> A1 & 1) {
+        if ((AX >> A1 & 1) && (c.wm >> A1 & 1)) {
             const float psi1 = c.l[A1] >= 0 ? pr1.x * psA1 + pr1.y * t1 : 0.f;
             if (own && c.l[A1] >= 0) p.psiH1[A1][1][c.s[A1]] = psi1;
             t1 += psi1;
         }
-        if (AX >> A2 & 1) {
+        if ((AX >> A2 & 1) && (c.wm >> A2 & 1)) {
             const float psi2 = c.l[A2] >= 0 ? pr2.x * psA2 + pr2.y * t2 : 0.f;
             if (own && c.l[A2] >= 0) p.psiH1[A2][0][c.s[A2]] = psi2;
             t2 += psi2;
@@ -175,12 +176,12 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float
     float t1 = hA2 - hA2m;
     float t2 = hA1 - hA1m;
     if (PML) {
-        if (AX >> A1 & 1) {
+        if ((AX >> A1 & 1) && (c.wm >> A1 & 1)) {
             const float psi1 = c.l[A1] >= 0 ? pr1.x * peA1 + pr1.y * t1 : 0.f;
             if (c.l[A1] >= 0) p.psiE[A1][1][c.s[A1]] = psi1;
             t1 += psi1;
         }
-        if (AX >> A2 & 1) {
+        if ((AX >> A2 & 1) && (c.wm >> A2 & 1)) {
             const float psi2 = c.l[A2] >= 0 ? pr2.x * peA2 + pr2.y * t2 : 0.f;
             if (c.l[A2] >= 0) p.psiE[A2][0][c.s[A2]] = psi2;
             t2 += psi2;
@@ -438,12 +439,14 @@ __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, fl
                                           float* e2)
 {
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
-    if ((AX >> A1 & 1) && p.cpml[A1]) {
+    // an axis whose slab no lane of the warp reaches is skipped: its
+    // consumers skip it too (Cell::wm), so the stale slots are never read
+    if ((AX >> A1 & 1) && (c.wm >> A1 & 1) && p.cpml[A1]) {
         const bool v = c.l[A1] >= 0;
         cp_async4z(d1, p.psiH0[A1][1] + c.s[A1], v);
         if (e1) cp_async4z(e1, p.psiE[A1][1] + c.s[A1], v);
     }
-    if ((AX >> A2 & 1) && p.cpml[A2]) {
+    if ((AX >> A2 & 1) && (c.wm >> A2 & 1) && p.cpml[A2]) {
         const bool v = c.l[A2] >= 0;
         cp_async4z(d2, p.psiH0[A2][0] + c.s[A2], v);
         if (e2) cp_async4z(e2, p.psiE[A2][0] + c.s[A2], v);
@@ -454,7 +457,7 @@ __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, fl
 // for the halo threads, their halo H cell (column geometry qh).
 template <int AX>
 __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, int b, int kk, int x0, int y0, int i,
-                                          int j, bool in, const PmlCol& qo, const PmlCol& qh, int tid)
+                                          int j, bool in, const PmlCol& qo, const PmlCol& qh, int tid, int wm_xy)
 {
     if (in) {
         Cell c;
@@ -462,6 +465,7 @@ __device__ __forceinline__ void psi_plane(const StepParams& p, PsiShared& ps, in
         c.j = j;
         c.k = kk;
         pml_cell(p, qo, c);
+        c.wm = wm_xy | (c.l[2] >= 0 ? 4 : 0);
         float(*o)[BX * BY] = ps.own[b];
         psi_fetch<0, AX>(p, c, &o[0][tid], &o[1][tid], &o[6][tid], &o[7][tid]);
         psi_fetch<1, AX>(p, c, &o[2][tid], &o[3][tid], &o[8][tid], &o[9][tid]);
@@ -557,6 +561,16 @@ constexpr unsigned TMA_TEST_EXTRA = 0;
 #endif
 
 struct NoPsi {};
+
+// CPML tiles skip the psi work of an axis in warps none of whose cells lies
+// in that axis' slab, and map the threads of x-slab tiles so that half of
+// their warps are clear of the slab (build option NLF_PML_NO_WARP_SKIP: every
+// warp does all of its tile's psi work, lanes along x)
+#ifdef NLF_PML_NO_WARP_SKIP
+constexpr bool kWarpSkip = false;
+#else
+constexpr bool kWarpSkip = true;
+#endif
 
 // Metal tiles: node divergences of P_f^n (difference units) on three planes,
 // plane q in slot q mod 3 (at plane k the z march reads planes k and k+1 and
@@ -766,12 +780,19 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
 {
     constexpr bool MET = MP >= 0;
     constexpr int NE = SM::kNE, NH = SM::kNH;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    // own cell of the thread: lanes along x, rows along y; in CPML tiles that
+    // reach an x slab each warp covers 16 columns of two rows instead, so
+    // that the warps of the half tile clear of the slab skip its psi work
+    constexpr bool XR = PML && (AX & 1) && kWarpSkip;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const int tx = XR ? ((tid & 15) + 16 * ((tid >> 5) & 1)) : (int)threadIdx.x;
+    const int ty = XR ? (2 * (tid >> 6) + ((tid >> 4) & 1)) : (int)threadIdx.y;
     const int i = x0 + tx, j = y0 + ty;
     const bool in = i < p.nx && j < p.ny;
     const int lx = tx + 4, ly = ty + 1;               // own cell in an E or H stage
     // CPML geometry of the own column and of the halo column (constant along z)
     PmlCol qo{}, qh{};
+    int wm_xy = 3;                                    // the warp's own cells reach the x (bit 0) / y (bit 1) slab
     if constexpr (PML) {
         qo = pml_col(p, i, j);
         if (tid < BY)
@@ -779,7 +800,11 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         else if (tid < BY + BX)
             qh = pml_col(p, x0 + tid - BY, y0 - 1);
         cpml_tables(p, sm.ps, x0, y0, tid);
+        if (kWarpSkip)
+            wm_xy = (__any_sync(0xffffffffu, in && qo.l0 >= 0) ? 1 : 0) |
+                    (__any_sync(0xffffffffu, in && qo.l1 >= 0) ? 2 : 0);
     }
+    const int wm_z = kWarpSkip ? 0 : 4;               // without the skip every axis is always on
     TmaRing<SM> r{sm, p, k0, x0, y0};
     if (tid == 0) {
         for (int q = 0; q < NE; ++q) mbar_init(&sm.barE[q]);
@@ -807,6 +832,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         float2 cx1{}, cx2{}, cy1{}, cy2{};
         if constexpr (PML) {
             pml_cell(p, qo, c);
+            c.wm = wm_xy | wm_z | (c.l[2] >= 0 ? 4 : 0);
             if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
             if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
             if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
@@ -820,7 +846,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         hy_prev = h_cell<1, PML, AX>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
                                  r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2, cy1, cy2);
     }
-    if constexpr (PML) psi_plane<AX>(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid);
+    if constexpr (PML) psi_plane<AX>(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid, wm_xy | wm_z);
     bool fail = __syncthreads_or(r.bad);
     if (!fail && tid == 0 && k0 + NE - 1 <= k1) r.issue_e(k0 + NE - 1);
     // metal tile: the planes of this chunk that hold material sites of the
@@ -899,7 +925,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         if constexpr (PML) {
             // psi of plane k+1 on its way while plane k is computed
             if (more) {
-                psi_plane<AX>(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, qo, qh, tid);
+                psi_plane<AX>(p, sm.ps, pb ^ 1, k + 1, x0, y0, i, j, in, qo, qh, tid, wm_xy | wm_z);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -913,7 +939,10 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         c.k = k;
         c.q = ((uint32_t)k * p.ny + j) * p.px + i;
         c.l[0] = c.l[1] = c.l[2] = -1;
-        if constexpr (PML) pml_cell(p, qo, c);
+        if constexpr (PML) {
+            pml_cell(p, qo, c);
+            c.wm = wm_xy | wm_z | (c.l[2] >= 0 ? 4 : 0);
+        }
         ZCoef uz{};
         if constexpr (PML) uz = zcoef(p, k);      // plane k's coefficients along z
         float hx = 0.f, hy = 0.f, hz = 0.f;

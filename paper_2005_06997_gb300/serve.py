@@ -4,20 +4,24 @@ Requests (problem dicts with an ``arrival_s`` time) arrive on a clock.  The
 server admits every arrived request whose state fits the HBM budget: it gets
 a torch device buffer bound with ``nlf_bind_state`` and its state stays on
 the device until it finishes.  Admission runs on a stream of its own while
-the GPU works on the current period.
+the GPU works.
 
-Scheduling, one DFT period (K * B time steps) at a time: the admitted
-requests are taken in order of remaining work (cells x remaining steps,
-smallest first) until their grids fill the GPU (``fill_cells``); those
-advance together in one ``nlf_batch_run`` call (a single grid runs alone
-through ``nlf_run``, the single-grid kernels).  Small grids, which leave
-most of the GPU idle on their own, share periods; a large grid runs alone,
-so small requests are not held to its step rate.  A request that has not
-advanced for ``max_wait_s`` joins the next period whatever its size, so
-large requests are not starved.  Requests that arrive while others run join
-at the next period boundary; finished requests are retired there, their
-spectra copied out and their memory returned.  ``cancel`` drops a waiting
-request or retires an admitted one at the next boundary.
+Scheduling, in two lanes on two streams that run concurrently, one DFT
+period (K * B time steps) at a time per lane:
+* the small lane takes the admitted requests whose grids are at most half
+  of ``fill_cells``, in order of remaining work (cells x remaining steps,
+  smallest first), until their grids fill ``fill_cells``; they advance
+  together in one ``nlf_batch_run`` call (small grids leave most of the GPU
+  idle on their own);
+* the large lane advances one larger request at a time through ``nlf_run``
+  (the single-grid kernels), the one with the least remaining work.
+A lane plans its next period as soon as its last one has finished, so small
+requests are never held to a large grid's step rate and large requests keep
+advancing while small ones come and go.  Within a lane a request that has
+not advanced for ``max_wait_s`` goes first.  Requests that arrive while
+others run join at their lane's next period; finished requests are retired
+there, their spectra copied out and their memory returned.  ``cancel`` drops
+a waiting request or retires an admitted one at its next period boundary.
 
 ``serve_fifo`` is the plain form for comparison: one request at a time, in
 arrival order, one grid per launch sequence.
@@ -83,17 +87,19 @@ def plan_period(active, now, fill_cells, max_wait_s):
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 256, stream=None, fill_cells: float = 16e6,
-                 max_wait_s: float = 1.0):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 256, stream=None, fill_cells: float = 4e6,
+                 max_wait_s: float = 1.5, period_b: int = 16):
         import torch
         nlfdtd.require_gpu()
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
         self.max_active = int(max_active)
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.stream2 = torch.cuda.Stream()
         self.init_stream = torch.cuda.Stream()
         self.fill_cells = float(fill_cells)
         self.max_wait_s = float(max_wait_s)
+        self.period_b = int(period_b)
         self.used = 0
         self.launches = 0
         self._cancel = set()
@@ -104,7 +110,7 @@ class Server:
         self._cancel.add(name)
 
     def _admit(self, req, now):
-        s = nlfdtd.Solver(req, block_b=SERVE_B)
+        s = nlfdtd.Solver(req, block_b=self.period_b)
         nb = s.state_bytes()
         buf = self.torch.empty(nb + 256, dtype=self.torch.uint8, device="cuda")
         ptr = (buf.data_ptr() + 255) // 256 * 256
@@ -124,7 +130,7 @@ class Server:
                 continue
             key = id(req)
             if key not in sizes:
-                probe = nlfdtd.Solver(req, block_b=SERVE_B)
+                probe = nlfdtd.Solver(req, block_b=self.period_b)
                 sizes[key] = probe.state_bytes()
                 probe.close()
             if sizes[key] > self.budget:
@@ -145,63 +151,101 @@ class Server:
         t0 = clock()
         sizes = {}
         torch = self.torch
+        lanes = [_Lane(self.stream, small=True), _Lane(self.stream2, small=False)]
         while pending or waiting or active:
             now = clock() - t0
             while pending and pending[0]["arrival_s"] <= now:
                 waiting.append(pending.popleft())
-            self._admit_waiting(waiting, active, sizes, now, results)
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
-                continue
-            U = _period(active[0])
-            run = plan_period(active, now, self.fill_cells, self.max_wait_s)
-            steps = [min(U, a.remaining) for a in run]
-            before = sum(a.solver.launches for a in run)
-            if len(run) == 1:
-                run[0].solver.run(steps[0], self.stream.cuda_stream)
-                status = [0]
-            else:
-                status = nlfdtd.batch_run([a.solver for a in run], steps, self.stream.cuda_stream)
-            done_ev = torch.cuda.Event()
-            done_ev.record(self.stream)
-            # host work while the GPU runs the period: admit new arrivals
-            while not done_ev.query():
+            if waiting:
+                self._admit_waiting(waiting, active, sizes, now, results)
+            # retire the work of lanes whose period has finished
+            for lane in lanes:
+                if lane.ev is not None and lane.ev.query():
+                    active = self._finish(lane, active, clock() - t0, results)
+            # cancelled requests that are not running leave now
+            busy = {id(a) for lane in lanes if lane.ev is not None for a in lane.run}
+            gone = {id(a) for a in active if id(a) not in busy and a.req.get("name") in self._cancel}
+            if gone:
                 now = clock() - t0
-                while pending and pending[0]["arrival_s"] <= now:
-                    waiting.append(pending.popleft())
-                if waiting:
-                    self._admit_waiting(waiting, active, sizes, now, results)
+                for a in active:
+                    if id(a) in gone:
+                        results.append(_result(a.req, a.admit_s, now, CANCELLED))
+                active = self._retire(active, gone)
+            # plan and launch the idle lanes
+            launched = False
+            for lane in lanes:
+                if lane.ev is not None:
+                    continue
+                free = [a for a in active if id(a) not in busy and (a.cells <= self.fill_cells / 2) == lane.small]
+                if not free:
+                    continue
+                if lane.small:
+                    run = plan_period(free, now, self.fill_cells, self.max_wait_s)
+                else:
+                    run = plan_period(free, now, 0.0, self.max_wait_s)[:1]
+                U = _period(run[0], self.period_b)
+                lane.run = run
+                lane.steps = [min(U, a.remaining) for a in run]
+                lane.before = sum(a.solver.launches for a in run)
+                if len(run) == 1:
+                    run[0].solver.run(lane.steps[0], lane.stream.cuda_stream)
+                    lane.status = [0]
+                else:
+                    lane.status = nlfdtd.batch_run([a.solver for a in run], lane.steps, lane.stream.cuda_stream)
+                lane.ev = torch.cuda.Event()
+                lane.ev.record(lane.stream)
+                busy.update(id(a) for a in run)
+                launched = True
+            if not launched:
+                if all(lane.ev is None for lane in lanes):
+                    if pending and not waiting:
+                        time.sleep(max(0.0, min(0.05, pending[0]["arrival_s"] - (clock() - t0))))
                 else:
                     time.sleep(0.0002)
-            self.launches += sum(a.solver.launches for a in run) - before
-            now = clock() - t0
-            done = set()
-            for a, n, st in zip(run, steps, status):
-                a.remaining -= n
-                a.last_run_s = now
-            for a, st in zip(run, status):
-                cancelled = a.req.get("name") in self._cancel
-                if st != 0 or a.remaining <= 0 or cancelled:
-                    code = CANCELLED if cancelled and st == 0 and a.remaining > 0 else int(st)
-                    res = _result(a.req, a.admit_s, now, code)
-                    if code == 0:
-                        res["spectra"] = a.solver.spectra()
-                    results.append(res)
-                    done.add(id(a))
-            # cancelled requests that did not run this period
-            for a in active:
-                if id(a) not in done and a.req.get("name") in self._cancel:
-                    results.append(_result(a.req, a.admit_s, now, CANCELLED))
-                    done.add(id(a))
-            for a in active:
-                if id(a) in done:
-                    self.used -= a.solver.state_bytes()
-                    a.solver.close()
-                    a.buf = None
-            active = [a for a in active if id(a) not in done]
         wall = clock() - t0
         return results, summarise(results, wall)
+
+    def _finish(self, lane, active, now, results):
+        """Account a lane's finished period; retire finished and cancelled
+        requests (also cancelled ones that did not run).  Returns the active
+        list without them."""
+        self.launches += sum(a.solver.launches for a in lane.run) - lane.before
+        done = set()
+        for a, n, st in zip(lane.run, lane.steps, lane.status):
+            a.remaining -= n
+            a.last_run_s = now
+            cancelled = a.req.get("name") in self._cancel
+            if st != 0 or a.remaining <= 0 or cancelled:
+                code = CANCELLED if cancelled and st == 0 and a.remaining > 0 else int(st)
+                res = _result(a.req, a.admit_s, now, code)
+                if code == 0:
+                    res["spectra"] = a.solver.spectra()
+                results.append(res)
+                done.add(id(a))
+        lane.ev = None
+        lane.run = []
+        return self._retire(active, done)
+
+    def _retire(self, active, done):
+        for a in active:
+            if id(a) in done:
+                self.used -= a.solver.state_bytes()
+                a.solver.close()
+                a.buf = None
+        return [a for a in active if id(a) not in done]
+
+
+class _Lane:
+    """One stream of the server and the period it has in flight."""
+
+    def __init__(self, stream, small):
+        self.stream = stream
+        self.small = small
+        self.ev = None
+        self.run = []
+        self.steps = []
+        self.status = []
+        self.before = 0
 
 
 def _result(req, admit_s, now, status):
@@ -210,17 +254,17 @@ def _result(req, admit_s, now, status):
             "cell_updates": float(np.prod(req["shape"])) * int(req["steps"])}
 
 
-# Samples buffered per DFT flush for served requests: a period is one DFT
-# period (K * SERVE_B steps), so this sets how often finished requests leave
-# and new ones join.
+# Samples buffered per DFT flush for served requests (the default of
+# Server.period_b): a period is one DFT period (K * B steps), so this sets
+# how often finished requests leave and new ones join.
 SERVE_B = 16
 
 
-def _period(a):
+def _period(a, b=SERVE_B):
     """Time steps of one DFT period of an active request (the scheduling unit)."""
     mon = a.req.get("monitors")
     K = mon.get("K", 16) if mon else 1
-    kb = K * SERVE_B
+    kb = K * b
     return kb if kb % 2 == 0 else 2 * kb
 
 

@@ -173,10 +173,23 @@ def config_cube_tips_512():
                            10000, (1.0, 5.0))
 
 
+def config_cube_tips_256():
+    """The 512^3 cube with tips at half size in every length (30 nm cube, tips
+    of 6 nm base, 5 nm height, 1.5 nm apex radius, 256^3 cells at 0.25 nm,
+    12-cell CPML, 5000 steps, 1-5 eV): the same kernels on a state of a few
+    GB, for profiler captures."""
+    n, dx = 256, 0.25e-9
+    sh = cube_tips_shape((n, n, n), 30e-9, 6e-9, 5e-9, 1.5e-9, dx)
+    reach = sh["side"] // 2 + sh["tip_height"]
+    return scatter_problem((n, n, n), dx, 12, [AU_LIKE_GNOR], [sh], ((n, n, n), (reach,) * 3),
+                           5000, (1.0, 5.0))
+
+
 CONFIGS = {
     "sphere_ag_r2nm_48": config_sphere_ag_48,
     "sphere_au_gnor_r10nm_224": config_sphere_au_gnor_224,
     "cube_tips_au_gnor_512": config_cube_tips_512,
+    "cube_tips_au_gnor_256": config_cube_tips_256,
 }
 
 

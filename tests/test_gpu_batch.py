@@ -1,5 +1,6 @@
-"""Batched stepping (nlf_batch_run): many uneven grids in one persistent launch
-per time step, against the same grids run alone and against the oracle."""
+"""Batched stepping (nlf_batch_run): many uneven grids advanced by one launch
+per kernel per time step over their joint work list, against the same grids
+run alone and against the oracle."""
 import copy
 import math
 
