@@ -396,7 +396,8 @@ def measure(name, n_steps, n_warmup, dist, dev, stream, e2e_reps, seg=None, tail
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": kb / (k_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": kb / (k_ms * 1e-3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "EM step: k_step + k_step_pml (concurrent), per time step",
+                     "kernel": "EM step: k_step and k_step_pml (concurrent), then k_step_metal where the "
+                               "material update is fused into the z march; per time step",
                      "kernel_ms": k_ms, "bytes_per_launch": kb},
         "whole_step": {"ms": ms_per_time_step, "bytes": sb,
                        "gbs": sb / (ms_per_time_step * 1e-3) / 1e9,

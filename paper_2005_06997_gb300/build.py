@@ -42,15 +42,21 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra=(), lib: str | None = None) -> str:
+    """Compile every translation unit (in parallel) and link the library.
+    `extra` adds nvcc flags (e.g. -DNLF_BOUNDS_CHECK=1 for the build whose
+    kernels check their global accesses); `lib` puts a variant library and
+    its objects elsewhere than the product's in-tree path (always rebuilt)."""
+    out = lib if lib is not None else LIB
+    if lib is None and not force and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    odir = os.path.dirname(out)
+    os.makedirs(odir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(odir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -64,12 +70,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             objs.append(obj)
             if verbose and log:
                 print(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = out + ".tmp%d" % os.getpid()
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -161,15 +161,17 @@ __global__ void k_dft_gather(const DftParams d, const float* __restrict__ E, con
     if (r > d.nrec) return;
     float e, h;
     if (r < d.nrec) {
-        e = __ldg(E + d.rec_e[r]);
-        const uint32_t o = d.rec_h[r];
-        h = 0.5f * (__ldg(H + o) + __ldg(H + o + d.rec_hs[r]));
+        const uint32_t oe = d.rec_e[r], o = d.rec_h[r], hs = d.rec_hs[r];
+        if (!(NLF_IN(d, 17, oe, d.nfield3) && NLF_IN(d, 18, (long long)o + hs, d.nfield3))) return;
+        e = __ldg(E + oe);
+        h = 0.5f * (__ldg(H + o) + __ldg(H + o + hs));
     } else {
         e = e_inc[d.inc_node];
         h = 0.5f * (h_inc[d.inc_node - 1] + h_inc[d.inc_node]);
         d.sample_step[slot] = *step;
     }
     const long long w = (long long)slot * (d.nrec + 1) + r;
+    if (!NLF_IN(d, 19, w, (long long)d.B * (d.nrec + 1))) return;
     d.sE[w] = e;
     d.sH[w] = h;
     if (!isfinite(e) || !isfinite(h)) atomicOr(err, 1);

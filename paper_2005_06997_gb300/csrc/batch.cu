@@ -44,15 +44,17 @@ __global__ void k_gather_batch(const BatchDft a, int slot)
     const DftParams& d = I.d;
     float e, h;
     if (r < d.nrec) {
-        e = __ldg(I.E[cur] + d.rec_e[r]);
-        const uint32_t o = d.rec_h[r];
-        h = 0.5f * (__ldg(I.H[cur] + o) + __ldg(I.H[cur] + o + d.rec_hs[r]));
+        const uint32_t oe = d.rec_e[r], o = d.rec_h[r], hs = d.rec_hs[r];
+        if (!(NLF_IN(d, 17, oe, d.nfield3) && NLF_IN(d, 18, (long long)o + hs, d.nfield3))) return;
+        e = __ldg(I.E[cur] + oe);
+        h = 0.5f * (__ldg(I.H[cur] + o) + __ldg(I.H[cur] + o + hs));
     } else {
         e = I.e_inc[cur][d.inc_node];
         h = 0.5f * (I.h_inc[cur][d.inc_node - 1] + I.h_inc[cur][d.inc_node]);
         d.sample_step[slot] = *I.step[cur];
     }
     const long long o = (long long)slot * (d.nrec + 1) + r;
+    if (!NLF_IN(d, 19, o, (long long)d.B * (d.nrec + 1))) return;
     d.sE[o] = e;
     d.sH[o] = h;
     if (!isfinite(e) || !isfinite(h)) atomicOr(I.err, 1);

@@ -64,9 +64,10 @@ constexpr double kMu0 = 1.25663706212e-6;
 
 struct Header {            // first bytes of the state buffer
     long long step[2];     // step counters, ping-pong by parity
-    int err;               // bit 0: non-finite sample seen
+    int err;               // bit 0: non-finite value; bit 2: a TMA wait gave up; bit 3: bounds (checked build)
     int cnt;               // pending DFT samples (host mirror, written before a save)
     long long n;           // time index (host mirror, written before a save)
+    nlf::BoundsRecord chk; // first out-of-bounds access of the bounds-checked build
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -643,6 +644,11 @@ void fill_params(nlf_ctx* c)
         p.step0 = &h->step[r];
         p.step1 = &h->step[w];
         p.err = &h->err;
+        p.chk = &h->chk;
+        p.nfield = c->nfield;
+        for (int a = 0; a < 3; ++a) p.psi_n[a] = c->pml_slab[a];
+        p.nbb = c->nbb;
+        p.ntiles_xy = c->tiles_x * c->tiles_y;
     }
     if (c->have_plane) {
         nlf::PlaneParams& m = c->pp;
@@ -683,6 +689,9 @@ void fill_params(nlf_ctx* c)
         d.omega = at<double>(c, c->off_omega);
         d.dt = c->dt;
         d.inc_node = c->inc_node;
+        d.nfield3 = 3 * c->nfield;
+        d.err = &at<Header>(c, c->off_hdr)->err;
+        d.chk = &at<Header>(c, c->off_hdr)->chk;
     }
 }
 
@@ -1637,10 +1646,13 @@ int nlf_sync(nlf_ctx* c, int timeout_ms)
             return fail(c, NLF_E_TIMEOUT, "work still running after %d ms", timeout_ms);
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    int err = 0;
-    CK(cudaMemcpy(&err, c->base + c->off_hdr + offsetof(Header, err), sizeof err, cudaMemcpyDeviceToHost));
-    if (err & 1) return fail(c, NLF_E_UNSTABLE, "non-finite field sample at time index %lld", c->n);
-    if (err & 4) return fail(c, NLF_E_CUDA, "a tensor-memory copy of the step kernel did not complete in time");
+    Header h{};
+    CK(cudaMemcpy(&h, c->base + c->off_hdr, sizeof h, cudaMemcpyDeviceToHost));
+    if (h.err & 8)
+        return fail(c, NLF_E_CUDA, "bounds check: access site %d index %lld outside [0, %lld) (%d accesses skipped)",
+                    h.chk.code, h.chk.idx, h.chk.lim, h.chk.hits);
+    if (h.err & 1) return fail(c, NLF_E_UNSTABLE, "non-finite field sample at time index %lld", c->n);
+    if (h.err & 4) return fail(c, NLF_E_CUDA, "a tensor-memory copy of the step kernel did not complete in time");
     return NLF_OK;
 }
 

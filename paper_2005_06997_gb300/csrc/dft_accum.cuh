@@ -44,10 +44,13 @@ __device__ __forceinline__ void accum_chunk(const DftParams& d, long long r0, in
         double2 ae[G], ah[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
+            ae[u] = ah[u] = make_double2(0.0, 0.0);
             if (g + u < rmax) {
                 const long long o = (r0 + g + u) * d.nf + f;
-                ae[u] = d.accE[o];
-                ah[u] = d.accH[o];
+                if (NLF_IN(d, 20, o, (d.nrec + 1) * d.nf)) {
+                    ae[u] = d.accE[o];
+                    ah[u] = d.accH[o];
+                }
             }
         }
         float er[G], ei[G], hr[G], hi[G];
@@ -69,7 +72,7 @@ __device__ __forceinline__ void accum_chunk(const DftParams& d, long long r0, in
         }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            if (g + u < rmax) {
+            if (g + u < rmax && NLF_IN(d, 20, (r0 + g + u) * d.nf + f, (d.nrec + 1) * d.nf)) {
                 const long long o = (r0 + g + u) * d.nf + f;
                 ae[u].x += (double)er[u];
                 ae[u].y += (double)ei[u];
@@ -96,7 +99,7 @@ __device__ __forceinline__ void accum_block(const DftParams& d, long long rb, in
     for (int q = t; q < B * ACC_NT; q += blockDim.x) {
         const int s = q / ACC_NT, u = q - s * ACC_NT;
         float2 v = make_float2(0.f, 0.f);
-        if (f0 + u < d.nf) {
+        if (f0 + u < d.nf && NLF_IN(d, 21, (long long)s * d.nf + f0 + u, (long long)d.B * d.nf)) {
             const float4 w = d.phase[s * d.nf + f0 + u];
             v = make_float2(w.x, w.y);
         }
@@ -114,8 +117,9 @@ __device__ __forceinline__ void accum_block(const DftParams& d, long long rb, in
         for (int q = t; q < B * RCH; q += blockDim.x) {
             const int s = q / RCH, rr = q - s * RCH;
             const long long r = r0 + rr;
-            sm.sE[s][rr] = r < nr ? d.sE[(long long)s * nr + r] : 0.f;
-            sm.sH[s][rr] = r < nr ? d.sH[(long long)s * nr + r] : 0.f;
+            const bool ok = r < nr && NLF_IN(d, 21, (long long)s * nr + r, (long long)d.B * nr);
+            sm.sE[s][rr] = ok ? d.sE[(long long)s * nr + r] : 0.f;
+            sm.sH[s][rr] = ok ? d.sH[(long long)s * nr + r] : 0.f;
         }
         __syncthreads();
         if (f < d.nf) accum_chunk<B, RCH>(d, r0, f, t, crf, srf, sm);

@@ -39,6 +39,34 @@
 
 namespace nlf {
 
+// Bounds-checked build (-DNLF_BOUNDS_CHECK): the non-TMA global accesses of
+// the step, material, TF/SF and DFT kernels are checked against the size of
+// their array; a violation raises bit 3 of the error word, the first one is
+// recorded (the access site's code, the index and the limit), and the access
+// is skipped (a load reads zero).  The product build compiles the checks out.
+struct BoundsRecord {
+    int code;
+    int hits;
+    long long idx, lim;
+};
+
+#ifdef NLF_BOUNDS_CHECK
+__device__ __forceinline__ bool nlf_in_bounds(int* err, BoundsRecord* rec, int code, long long idx, long long lim)
+{
+    if (idx >= 0 && idx < lim) return true;
+    if (err) atomicOr(err, 8);
+    if (rec && atomicCAS(&rec->code, 0, code) == 0) {
+        rec->idx = idx;
+        rec->lim = lim;
+    }
+    if (rec) atomicAdd(&rec->hits, 1);
+    return false;
+}
+#define NLF_IN(P, CODE, IDX, LIM) ::nlf::nlf_in_bounds((P).err, (P).chk, (CODE), (long long)(IDX), (long long)(LIM))
+#else
+#define NLF_IN(P, CODE, IDX, LIM) true
+#endif
+
 // The CPML slab axes that the cell box [lo, hi] (inclusive) reaches, bit a
 // for axis a (0: clear of every slab).
 __host__ __device__ __forceinline__ int pml_axes_of_box(const int n3[3], const int cpml[3], int pml, const int lo[3],
@@ -160,6 +188,13 @@ struct StepParams {
     const long long* step0;
     long long* step1;
     int* err;
+    // array sizes for the bounds-checked build: floats per field component,
+    // per psi slot of each CPML axis, cells of the metal box, tile columns
+    long long nfield;
+    long long psi_n[3];
+    long long nbb;
+    int ntiles_xy;
+    BoundsRecord* chk;
 };
 
 struct VoxParams {
@@ -226,6 +261,9 @@ struct DftParams {
     const double* omega;
     double dt;
     int inc_node;
+    long long nfield3;          // floats of the three components of E (and of H): bounds-checked build
+    int* err;
+    BoundsRecord* chk;
 };
 
 // Batched stepping: instance q uses params[2 q + (base_par ^ launch parity)].

@@ -148,17 +148,17 @@ __device__ __forceinline__ float h_cell(const StepParams& p, const Cell& c, floa
         // AX: the slab axes the tile touches (compile time); others have no psi here
         if ((AX >> A1 & 1) && (c.wm >> A1 & 1)) {
             const float psi1 = c.l[A1] >= 0 ? pr1.x * psA1 + pr1.y * t1 : 0.f;
-            if (own && c.l[A1] >= 0) p.psiH1[A1][1][c.s[A1]] = psi1;
+            if (own && c.l[A1] >= 0 && NLF_IN(p, 3, c.s[A1], p.psi_n[A1])) p.psiH1[A1][1][c.s[A1]] = psi1;
             t1 += psi1;
         }
         if ((AX >> A2 & 1) && (c.wm >> A2 & 1)) {
             const float psi2 = c.l[A2] >= 0 ? pr2.x * psA2 + pr2.y * t2 : 0.f;
-            if (own && c.l[A2] >= 0) p.psiH1[A2][0][c.s[A2]] = psi2;
+            if (own && c.l[A2] >= 0 && NLF_IN(p, 3, c.s[A2], p.psi_n[A2])) p.psiH1[A2][0][c.s[A2]] = psi2;
             t2 += psi2;
         }
     }
     const float h = h0 - p.S * (t1 - t2);
-    if (own) p.H1[C][c.q] = h;
+    if (own && NLF_IN(p, 2, c.q, p.nfield)) p.H1[C][c.q] = h;
     return h;
 }
 
@@ -178,16 +178,16 @@ __device__ __forceinline__ void e_cell(const StepParams& p, const Cell& c, float
     if (PML) {
         if ((AX >> A1 & 1) && (c.wm >> A1 & 1)) {
             const float psi1 = c.l[A1] >= 0 ? pr1.x * peA1 + pr1.y * t1 : 0.f;
-            if (c.l[A1] >= 0) p.psiE[A1][1][c.s[A1]] = psi1;
+            if (c.l[A1] >= 0 && NLF_IN(p, 4, c.s[A1], p.psi_n[A1])) p.psiE[A1][1][c.s[A1]] = psi1;
             t1 += psi1;
         }
         if ((AX >> A2 & 1) && (c.wm >> A2 & 1)) {
             const float psi2 = c.l[A2] >= 0 ? pr2.x * peA2 + pr2.y * t2 : 0.f;
-            if (c.l[A2] >= 0) p.psiE[A2][0][c.s[A2]] = psi2;
+            if (c.l[A2] >= 0 && NLF_IN(p, 4, c.s[A2], p.psi_n[A2])) p.psiE[A2][0][c.s[A2]] = psi2;
             t2 += psi2;
         }
     }
-    p.E1[C][c.q] = En + p.Sb * (t1 - t2);
+    if (NLF_IN(p, 5, c.q, p.nfield)) p.E1[C][c.q] = En + p.Sb * (t1 - t2);
 }
 
 // Node divergence of P_f^n (difference units) at bbox-local offset b.
@@ -223,6 +223,7 @@ __device__ __forceinline__ float site_update(const StepParams& p, uint32_t b, in
         acs += ac[pp];
     }
     const float delta = (p.S * curl - af - acs - mG * gd - m.cE * En) * m.inv_den;
+    if (!NLF_IN(p, 11, b, p.nbb)) return En + delta;
     if (m.free_e) {
         const float dP = af + m.D3 * (3.f * En + delta) + mG * gd;
         p.P1[C][b] = p_old + dP;
@@ -256,11 +257,15 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
     constexpr int A1 = (C + 1) % 3, A2 = (C + 2) % 3;
     const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
     const uint32_t st[3] = {1u, (uint32_t)p.px, (uint32_t)p.px * (uint32_t)p.ny};
+    const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
+    if (!(NLF_IN(p, 13, q, p.nfield) && NLF_IN(p, 13, (long long)q - st[A1], p.nfield) &&
+          NLF_IN(p, 13, (long long)q - st[A2], p.nfield) && NLF_IN(p, 14, b + stb, p.nbb) &&
+          NLF_IN(p, 14, (long long)b - sz, p.nbb)))
+        return;
     const int id = __ldg(p.mat[C] + b);
     const float h2 = p.H1[A2][q], h2m = p.H1[A2][q - st[A1]];
     const float h1 = p.H1[A1][q], h1m = p.H1[A1][q - st[A2]];
     const float En = __ldg(p.E0[C] + q);
-    const uint32_t stb = C == 0 ? 1u : (C == 1 ? sy : sz);
     const float gd_raw = node_div(p, b + stb, sy, sz) - node_div(p, b, sy, sz);
     const float p_old = __ldg(p.P0[C] + b);
     const float af_raw = p.auxf[C][b];
@@ -279,8 +284,8 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
         const uint32_t bi = b % (uint32_t)p.bb_n[0], r = b / (uint32_t)p.bb_n[0];
         const uint32_t bj = r % (uint32_t)p.bb_n[1], bk = r / (uint32_t)p.bb_n[1];
         Cell c = make_cell(p, p.bb_lo[0] + (int)bi, p.bb_lo[1] + (int)bj, p.bb_lo[2] + (int)bk, true);
-        if (c.l[A1] >= 0) t1 += p.psiE[A1][1][c.s[A1]];
-        if (c.l[A2] >= 0) t2 += p.psiE[A2][0][c.s[A2]];
+        if (c.l[A1] >= 0 && NLF_IN(p, 15, c.s[A1], p.psi_n[A1])) t1 += p.psiE[A1][1][c.s[A1]];
+        if (c.l[A2] >= 0 && NLF_IN(p, 15, c.s[A2], p.psi_n[A2])) t2 += p.psiE[A2][0][c.s[A2]];
     }
     const float curl = t1 - t2;
     p.E1[C][q] = site_update<C, NLF_MAX_POLES>(p, b, id, En, curl, gd_raw, p_old, af_raw, g1, pc, ac, PMLS);
@@ -309,7 +314,7 @@ __device__ __forceinline__ void metal_entry(const StepParams& p, long long t)
         metal_site<2>(p, b, q);
 }
 
-__global__ void __launch_bounds__(256) k_metal(const StepParams p, long long n_sites)
+__global__ void __launch_bounds__(256, 6) k_metal(const StepParams p, long long n_sites)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n_sites) metal_entry(p, t);
@@ -442,12 +447,12 @@ __device__ __forceinline__ void psi_fetch(const StepParams& p, const Cell& c, fl
     // an axis whose slab no lane of the warp reaches is skipped: its
     // consumers skip it too (Cell::wm), so the stale slots are never read
     if ((AX >> A1 & 1) && (c.wm >> A1 & 1) && p.cpml[A1]) {
-        const bool v = c.l[A1] >= 0;
+        const bool v = c.l[A1] >= 0 && NLF_IN(p, 7, c.s[A1], p.psi_n[A1]);
         cp_async4z(d1, p.psiH0[A1][1] + c.s[A1], v);
         if (e1) cp_async4z(e1, p.psiE[A1][1] + c.s[A1], v);
     }
     if ((AX >> A2 & 1) && (c.wm >> A2 & 1) && p.cpml[A2]) {
-        const bool v = c.l[A2] >= 0;
+        const bool v = c.l[A2] >= 0 && NLF_IN(p, 7, c.s[A2], p.psi_n[A2]);
         cp_async4z(d2, p.psiH0[A2][0] + c.s[A2], v);
         if (e2) cp_async4z(e2, p.psiE[A2][0] + c.s[A2], v);
     }
@@ -724,6 +729,7 @@ __device__ __forceinline__ uint32_t site_ids(const StepParams& p, bool in, int b
     const int bk = k - p.bb_lo[2];
     if (!in || bi < 0 || bj < 0 || bk < 0 || bi >= p.bb_n[0] || bj >= p.bb_n[1] || bk >= p.bb_n[2]) return 0u;
     const uint32_t b = ((uint32_t)bk * (uint32_t)p.bb_n[1] + (uint32_t)bj) * (uint32_t)p.bb_n[0] + (uint32_t)bi;
+    if (!NLF_IN(p, 8, b, p.nbb)) return 0u;
     return (uint32_t)__ldg(p.mat[0] + b) | ((uint32_t)__ldg(p.mat[1] + b) << 8) |
            ((uint32_t)__ldg(p.mat[2] + b) << 16);
 }
@@ -742,6 +748,11 @@ __device__ __forceinline__ void div_load(const StepParams& p, int i, int j, int 
     }
     const uint32_t sy = (uint32_t)p.bb_n[0], sz = (uint32_t)p.bb_n[0] * (uint32_t)p.bb_n[1];
     const uint32_t b = (uint32_t)bk * sz + (uint32_t)bj * sy + (uint32_t)bi;
+    if (!(NLF_IN(p, 9, b, p.nbb) && NLF_IN(p, 9, (long long)b - sz, p.nbb))) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = 0.f;
+        return;
+    }
     v[0] = __ldg(p.P0[0] + b);
     v[1] = __ldg(p.P0[0] + b - 1);
     v[2] = __ldg(p.P0[1] + b);
@@ -833,17 +844,18 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         if constexpr (PML) {
             pml_cell(p, qo, c);
             c.wm = wm_xy | wm_z | (c.l[2] >= 0 ? 4 : 0);
-            if (c.l[1] >= 0) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
-            if (c.l[2] >= 0) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
-            if (c.l[2] >= 0) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
-            if (c.l[0] >= 0) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
+            if (c.l[1] >= 0 && NLF_IN(p, 6, c.s[1], p.psi_n[1])) px1 = __ldg(p.psiH0[1][1] + c.s[1]);
+            if (c.l[2] >= 0 && NLF_IN(p, 6, c.s[2], p.psi_n[2])) px2 = __ldg(p.psiH0[2][0] + c.s[2]);
+            if (c.l[2] >= 0 && NLF_IN(p, 6, c.s[2], p.psi_n[2])) py1 = __ldg(p.psiH0[2][1] + c.s[2]);
+            if (c.l[0] >= 0 && NLF_IN(p, 6, c.s[0], p.psi_n[0])) py2 = __ldg(p.psiH0[0][0] + c.s[0]);
             const ZCoef zp = zcoef(p, k0 - 1);
             cpml_pair<0>(sm.ps, 2, tx + 1, ty + 1, zp, cx1, cx2);
             cpml_pair<1>(sm.ps, 2, tx + 1, ty + 1, zp, cy1, cy2);
         }
-        hx_prev = h_cell<0, PML, AX>(p, c, __ldg(p.H0[0] + c.q), r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
+        const bool qok = NLF_IN(p, 1, c.q, p.nfield);
+        hx_prev = h_cell<0, PML, AX>(p, c, qok ? __ldg(p.H0[0] + c.q) : 0.f, r.e(pm, 2, ly, lx), r.e(pm, 2, ly + 1, lx),
                                  r.e(pm, 1, ly, lx), r.e(k0, 1, ly, lx), false, px1, px2, cx1, cx2);
-        hy_prev = h_cell<1, PML, AX>(p, c, __ldg(p.H0[1] + c.q), r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
+        hy_prev = h_cell<1, PML, AX>(p, c, qok ? __ldg(p.H0[1] + c.q) : 0.f, r.e(pm, 0, ly, lx), r.e(k0, 0, ly, lx),
                                  r.e(pm, 2, ly, lx), r.e(pm, 2, ly, lx + 1), false, py1, py2, cy1, cy2);
     }
     if constexpr (PML) psi_plane<AX>(p, sm.ps, 0, k0, x0, y0, i, j, in, qo, qh, tid, wm_xy | wm_z);
@@ -856,7 +868,8 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
     uint32_t idn = 0;
     bool prev_mp = false;
     if constexpr (MET) {
-        const int2 kr = p.tile_kr[(y0 / BY) * p.tiles_x + x0 / BX];
+        const int tix = (y0 / BY) * p.tiles_x + x0 / BX;
+        const int2 kr = NLF_IN(p, 12, tix, p.ntiles_xy) ? p.tile_kr[tix] : make_int2(0, 0);
         kmin = max(p.nz - kr.x, k0);
         kmax = min(kr.y - 1, k1 - 1);
         mbi = i - p.bb_lo[0];
@@ -895,6 +908,7 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                 if (ids) {
                     const int bk = k - p.bb_lo[2];
                     bsite = ((uint32_t)bk * (uint32_t)p.bb_n[1] + (uint32_t)mbj) * (uint32_t)p.bb_n[0] + (uint32_t)mbi;
+                    if (!NLF_IN(p, 10, bsite, p.nbb)) ids = 0u;
 #pragma unroll
                     for (int C = 0; C < 3; ++C) {
                         if (!((ids >> (8 * C)) & 0xffu)) continue;
@@ -1037,17 +1051,17 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                 if (j >= 1 && k >= 1)
                     e_cell<0, PML, AX>(p, c, ex, hz, hzm, hy, hy_prev, PML ? po[6 * S] : 0.f, PML ? po[7 * S] : 0.f,
                                    c1, c2);
-                else
+                else if (NLF_IN(p, 5, c.q, p.nfield))
                     p.E1[0][c.q] = 0.f;
                 if (i >= 1 && k >= 1)
                     e_cell<1, PML, AX>(p, c, ey, hx, hx_prev, hz, hzi, PML ? po[8 * S] : 0.f, PML ? po[9 * S] : 0.f,
                                    d1, d2);
-                else
+                else if (NLF_IN(p, 5, c.q, p.nfield))
                     p.E1[1][c.q] = 0.f;
                 if (i >= 1 && j >= 1)
                     e_cell<2, PML, AX>(p, c, ez, hy, hyi, hx, hxm, PML ? po[10 * S] : 0.f, PML ? po[11 * S] : 0.f,
                                    e1, e2);
-                else
+                else if (NLF_IN(p, 5, c.q, p.nfield))
                     p.E1[2][c.q] = 0.f;
             } else {
                 const float cx = (hz - hzm) - (hy - hy_prev);
@@ -1074,9 +1088,11 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
                                                    so_g[2], so_c[2], so_q[2]);
                     }
                 }
-                p.E1[0][c.q] = nx;
-                p.E1[1][c.q] = ny;
-                p.E1[2][c.q] = nz;
+                if (NLF_IN(p, 5, c.q, p.nfield)) {
+                    p.E1[0][c.q] = nx;
+                    p.E1[1][c.q] = ny;
+                    p.E1[2][c.q] = nz;
+                }
             }
         }
         hx_prev = hx;
@@ -1118,7 +1134,9 @@ enum { TILE_BG = 0, TILE_PML = 1, TILE_MET = 2 };
 __device__ __forceinline__ bool metal_tile(const StepParams& p, int bx, int by, int k0, int k1)
 {
     if (!p.fuse_metal) return false;
-    const int2 kr = p.tile_kr[by * p.tiles_x + bx];
+    const int tix = by * p.tiles_x + bx;
+    if (!NLF_IN(p, 12, tix, p.ntiles_xy)) return false;
+    const int2 kr = p.tile_kr[tix];
     return p.nz - kr.x < k1 && kr.y - 1 >= k0;
 }
 
@@ -1359,7 +1377,7 @@ __device__ __forceinline__ void tfsf_item(const StepParams& p, long long t)
         return;
     const uint32_t q = ((uint32_t)k * p.ny + j) * p.px + i;
     float* f = isH ? p.H1[comp] : p.E1[comp];
-    f[q] += v;
+    if (NLF_IN(p, 16, q, p.nfield)) f[q] += v;
 }
 
 __global__ void __launch_bounds__(256) k_tfsf(const StepParams p, long long n)
@@ -1373,7 +1391,7 @@ __global__ void __launch_bounds__(256) k_tfsf(const StepParams p, long long n)
 // cells (material sites lie at least two cells inside the TF surface), so no
 // order between them is needed, and the short TF/SF blocks fill the SMs the
 // material blocks leave at the end of the launch.
-__global__ void __launch_bounds__(256) k_post(const StepParams p, long long n_sites, long long nb_metal, long long n_tf)
+__global__ void __launch_bounds__(256, 8) k_post(const StepParams p, long long n_sites, long long nb_metal, long long n_tf)
 {
     const long long bx = blockIdx.x;
     if (bx < nb_metal) {
