@@ -140,6 +140,8 @@ struct nlf_ctx {
     cudaStream_t cap = nullptr;         // private stream for graph capture
     cudaStream_t aux = nullptr;         // second stream of the step: the CPML tiles
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t aux2 = nullptr;        // third stream of the step: the metal tiles
+    cudaEvent_t join2 = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long gnodes = 0;
     long long n = 0;                    // time index
@@ -443,12 +445,17 @@ int plan(nlf_ctx* c)
 #ifdef NLF_NO_FUSE
     c->fuse = false;                  // build option: every material site on the site-list kernel
 #else
-    // fused when the metal box is a quarter of the grid or more: a smaller
+    // fused when the metal box is a quarter of the grid or more (build option
+    // NLF_FUSE_FRAC: fused when FRAC x box cells >= grid cells): a smaller
     // particle gives the metal kernel too few tiles to fill the GPU, and the
     // site-list kernel is then faster (224^3 sphere, 10 % of the cells in its
-    // box: 0.185 against 0.204 ms per step; 512^3 cube, 25 %: 2.10 against
-    // 1.91); contexts with more than one critical-point pole are not fused
-    c->fuse = c->has_metal && c->max_poles <= 1 && 4 * c->nbb >= c->ncell;
+    // box: 0.181 against 0.190 ms per step fused; 512^3 cube, 25 %: 2.10
+    // against 1.83); contexts with more than one critical-point pole are not
+    // fused
+#ifndef NLF_FUSE_FRAC
+#define NLF_FUSE_FRAC 4
+#endif
+    c->fuse = c->has_metal && c->max_poles <= 1 && (long long)NLF_FUSE_FRAC * c->nbb >= c->ncell;
 #endif
     if (c->has_metal) {
         const size_t nb = (size_t)c->nbb;
@@ -903,18 +910,33 @@ int ensure_ready(nlf_ctx* c, cudaStream_t st)
     if (!c->aux) CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
     if (!c->fork) CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     if (!c->join) CK(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+    if (!c->aux2) CK(cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking));
+    if (!c->join2) CK(cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming));
     return initialise(c, st);
 }
 
 void monitor_work(nlf_ctx* c, cudaStream_t st);
 
 // The EM step of time step n on st: with CPML tiles, their kernel runs on the
-// context's second stream concurrently with the other tiles' kernel, forked
-// from and joined back into st (a fork / join inside a captured graph too).
+// context's second stream and, with fused metal tiles, the metal kernel on
+// its third, concurrently with the other tiles' kernel, forked from and
+// joined back into st (a fork / join inside a captured graph too).
 void launch_em(nlf_ctx* c, cudaStream_t st)
 {
     const nlf::StepParams& sp = c->sp[c->n & 1];
     const bool pml = nlf::step_has_pml(sp);
+    const bool met = c->fuse && c->n_msites > c->n_psites;
+#ifndef NLF_METAL_AFTER
+    // the metal tiles on a third stream beside the others (512^3 cube: 1.833
+    // against 1.859 ms per step with the metal kernel after them)
+    if (met) {
+        cudaEventRecord(c->fork, st);
+        cudaStreamWaitEvent(c->aux2, c->fork, 0);
+        nlf::launch_step_metal(sp, c->aux2);
+        cudaEventRecord(c->join2, c->aux2);
+        c->launches += 1;
+    }
+#endif
     if (pml) {
         cudaEventRecord(c->fork, st);
         cudaStreamWaitEvent(c->aux, c->fork, 0);
@@ -927,13 +949,15 @@ void launch_em(nlf_ctx* c, cudaStream_t st)
         nlf::launch_step(sp, st);
         c->launches += 1;
     }
-    // the metal tiles after the others, alone on the GPU (run beside them,
-    // the three kernels' streams contend for L2 and the step takes longer
-    // than the three in sequence: 2.05 against 1.92 ms on the 512^3 cube)
-    if (c->fuse && c->n_msites > c->n_psites) {
+#ifndef NLF_METAL_AFTER
+    if (met) cudaStreamWaitEvent(st, c->join2, 0);
+#else
+    // build option: the metal tiles after the others
+    if (met) {
         nlf::launch_step_metal(sp, st);
         c->launches += 1;
     }
+#endif
 }
 
 // The work after the EM step of time step n: the TF/SF corrections and the
@@ -1973,6 +1997,8 @@ void nlf_destroy(nlf_ctx* c)
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->fork) cudaEventDestroy(c->fork);
     if (c->join) cudaEventDestroy(c->join);
+    if (c->aux2) cudaStreamDestroy(c->aux2);
+    if (c->join2) cudaEventDestroy(c->join2);
     if (c->owned && c->base) cudaFree(c->base);
     delete c;
 }
