@@ -55,6 +55,7 @@ void launch_gather_batch(const BatchDft& a, long long total_records, int slot, c
 void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
                         int count, cudaStream_t st);
 int step_kz(const StepParams& p);
+int step_chunks(const StepParams& p, int kz);
 }  // namespace nlf
 
 namespace {
@@ -845,6 +846,8 @@ int initialise(nlf_ctx* c, cudaStream_t st)
             tmp.nx = c->g.nx;
             tmp.ny = c->g.ny;
             tmp.nz = c->g.nz;
+            for (int a = 0; a < 3; ++a) tmp.cpml[a] = sg.cpml[a];
+            tmp.pml = sg.pml;
             sg.tile_kr = nullptr;
             sg.only_pml = 1;
             sg.kz = nlf::step_kz(tmp);
@@ -1124,7 +1127,7 @@ int plan_descriptors(BatchPlan* P, int kz)
         b.tiles_x = (x->g.nx + 31) / 32;
         b.tiles_y = (x->g.ny + 7) / 8;
         b.kz = kz > 0 ? kz : nlf::step_kz(x->sp[0]);
-        b.chunks = (x->g.nz + b.kz - 1) / b.kz;
+        b.chunks = nlf::step_chunks(x->sp[0], b.kz);
         b.base_par = P->par[q];
         it += (long long)b.tiles_x * b.tiles_y * b.chunks;
         item_end[q] = it;

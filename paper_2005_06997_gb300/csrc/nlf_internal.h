@@ -28,7 +28,7 @@
 #define NLF_SITE_IN_CPML (1u << 29)          // the site's cell lies in a CPML slab
 #define NLF_SITE_OFFSET_MASK ((1u << 29) - 1u)
 // Tiles of the EM z-march: BX x BY columns of cells, marched along z in
-// chunks of kz planes
+// chunks (zchunk_range)
 #define NLF_TILE_BX 32
 #define NLF_TILE_BY 8
 #define NLF_INC_PML 40          // CPML cells at the far end of the 1D incident grid
@@ -79,13 +79,63 @@ __host__ __device__ __forceinline__ int pml_axes_of_box(const int n3[3], const i
     return m;
 }
 
+// The z chunks of the EM z-march.  Without a CPML along z: chunks of kz
+// planes from plane 0.  With one (and room between the slabs): the bottom
+// chunk holds the slab and one plane more, [0, pml + 1), the top chunk
+// likewise [nz - pml - 1, nz), and the planes between are cut into chunks of
+// kz (the last may be shorter).  The interior chunks' halo planes (k0 - 1
+// below, k1 above) then lie outside the slabs, so only the two end chunks
+// run the CPML code along z.
+__host__ __device__ __forceinline__ bool zchunk_aligned(int nz, int cpml_z, int pml)
+{
+    return cpml_z && nz - 2 * (pml + 1) >= 1;
+}
+
+__host__ __device__ __forceinline__ int zchunk_count(int nz, int cpml_z, int pml, int kz)
+{
+    if (!zchunk_aligned(nz, cpml_z, pml)) return (nz + kz - 1) / kz;
+    return 2 + (nz - 2 * (pml + 1) + kz - 1) / kz;
+}
+
+// Planes [k0, k1) of chunk c (0 <= c < zchunk_count).
+__host__ __device__ __forceinline__ void zchunk_range(int nz, int cpml_z, int pml, int kz, int c, int& k0, int& k1)
+{
+    if (!zchunk_aligned(nz, cpml_z, pml)) {
+        k0 = c * kz;
+        k1 = k0 + kz < nz ? k0 + kz : nz;
+        return;
+    }
+    const int zl = pml + 1, zh = nz - pml - 1;
+    if (c == 0) {
+        k0 = 0;
+        k1 = zl;
+    } else if (c == zchunk_count(nz, cpml_z, pml, kz) - 1) {
+        k0 = zh;
+        k1 = nz;
+    } else {
+        k0 = zl + (c - 1) * kz;
+        k1 = k0 + kz < zh ? k0 + kz : zh;
+    }
+}
+
+// The chunk that holds plane k.
+__host__ __device__ __forceinline__ int zchunk_of(int nz, int cpml_z, int pml, int kz, int k)
+{
+    if (!zchunk_aligned(nz, cpml_z, pml)) return k / kz;
+    const int zl = pml + 1, zh = nz - pml - 1;
+    if (k < zl) return 0;
+    if (k >= zh) return zchunk_count(nz, cpml_z, pml, kz) - 1;
+    return 1 + (k - zl) / kz;
+}
+
 // Does the tile holding cell (i, j, k) reach a CPML slab (its one-cell halo
-// included)?  Tiles are NLF_TILE_BX x NLF_TILE_BY x kz.
+// included)?  Tiles are NLF_TILE_BX x NLF_TILE_BY x (a z chunk).
 __host__ __device__ __forceinline__ bool cell_in_pml_tile(const int n3[3], const int cpml[3], int pml, int kz, int i,
                                                           int j, int k)
 {
-    const int x0 = i / NLF_TILE_BX * NLF_TILE_BX, y0 = j / NLF_TILE_BY * NLF_TILE_BY, k0 = k / kz * kz;
-    const int k1 = k0 + kz < n3[2] ? k0 + kz : n3[2];
+    const int x0 = i / NLF_TILE_BX * NLF_TILE_BX, y0 = j / NLF_TILE_BY * NLF_TILE_BY;
+    int k0 = 0, k1 = 0;
+    zchunk_range(n3[2], cpml[2], pml, kz, zchunk_of(n3[2], cpml[2], pml, kz, k), k0, k1);
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + NLF_TILE_BX, y0 + NLF_TILE_BY, k1};
     return pml_axes_of_box(n3, cpml, pml, lo, hi) != 0;

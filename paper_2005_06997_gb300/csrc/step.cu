@@ -1140,26 +1140,30 @@ __device__ __forceinline__ bool metal_tile(const StepParams& p, int bx, int by, 
     return p.nz - kr.x < k1 && kr.y - 1 >= k0;
 }
 
-// The metal kernel marches the planes that k_step leaves to it (the chunks of
-// kz planes that hold material sites of the tile column) in sub-chunks of
-// kzm planes (kzm divides kz): more, shorter marches for its heavier planes.
-// Returns false if sub-chunk bzm of tile (bx, by) is not one of them.
+// The metal kernel marches the planes that k_step leaves to it (the chunks
+// that hold material sites of the tile column) in sub-chunks of kzm planes
+// (kzm divides kz, so kz / kzm sub-chunks cover an interior chunk): more,
+// shorter marches for its heavier planes.  Returns false if sub-chunk bzm of
+// tile (bx, by) is not one of them; [c0, c1) is the chunk that holds it.
 __device__ __forceinline__ bool metal_subchunk(const StepParams& p, int bx, int by, int bzm, int kz, int kzm, int& k0,
-                                               int& k1)
+                                               int& k1, int& c0, int& c1)
 {
-    k0 = bzm * kzm;
-    k1 = min(k0 + kzm, p.nz);
-    const int c0 = k0 / kz * kz, c1 = min(c0 + kz, p.nz);     // the k_step chunk holding it
-    return metal_tile(p, bx, by, c0, c1);
+    const int per = kz / kzm;
+    zchunk_range(p.nz, p.cpml[2], p.pml, kz, bzm / per, c0, c1);
+    k0 = c0 + (bzm % per) * kzm;
+    k1 = min(k0 + kzm, c1);
+    return k0 < c1 && metal_tile(p, bx, by, c0, c1);
 }
 
 template <int KIND, int MP, class SM>
 __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm, int kzm = 0)
 {
     const int x0 = bx * BX, y0 = by * BY;
-    int k0 = bz * kz, k1 = min(k0 + kz, p.nz);
+    int k0 = 0, k1 = 0, c0 = 0, c1 = 0;
     if constexpr (KIND == TILE_MET) {
-        if (!metal_subchunk(p, bx, by, bz, kz, kzm, k0, k1)) return;
+        if (!metal_subchunk(p, bx, by, bz, kz, kzm, k0, k1, c0, c1)) return;
+    } else {
+        zchunk_range(p.nz, p.cpml[2], p.pml, kz, bz, k0, k1);
     }
     const int lo[3] = {x0 - 1, y0 - 1, k0 - 1};
     const int hi[3] = {x0 + BX, y0 + BY, k1};
@@ -1176,7 +1180,6 @@ __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by
             march_tma<true, 7>(p, x0, y0, k0, k1, sm);
     } else if constexpr (KIND == TILE_MET) {
         // the chunk's PML class is that of k_step's chunk, which holds the sub-chunk
-        const int c0 = k0 / kz * kz, c1 = min(c0 + kz, p.nz);
         const int clo[3] = {x0 - 1, y0 - 1, c0 - 1};
         const int chi[3] = {x0 + BX, y0 + BY, c1};
         if (tile_pml_axes(p, clo, chi) == 0) march_tma<false, 0, SM, MP>(p, x0, y0, k0, k1, sm);
@@ -1516,12 +1519,14 @@ void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t 
     k_metal_batch<<<(unsigned)g, 256, 0, st>>>(a);
 }
 
+int step_chunks(const StepParams& p, int kz) { return zchunk_count(p.nz, p.cpml[2], p.pml, kz); }
+
 int step_kz(const StepParams& p)
 {
     // z chunk: enough blocks for several waves over 152 SMs, few chunk prologues
     const long long tiles = (long long)((p.nx + BX - 1) / BX) * ((p.ny + BY - 1) / BY);
     int kz = 32;
-    while (kz > 8 && tiles * ((p.nz + kz - 1) / kz) < 4 * 152 * 4) kz /= 2;
+    while (kz > 8 && tiles * step_chunks(p, kz) < 4 * 152 * 4) kz /= 2;
     return kz;
 }
 
@@ -1551,7 +1556,7 @@ void launch_step(const StepParams& p, cudaStream_t st)
 {
     const int kz = step_kz(p);
     dim3 blk(BX, BY, 1);
-    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, step_chunks(p, kz));
     k_step<<<grd, blk, 0, st>>>(p, kz);
 }
 
@@ -1560,7 +1565,7 @@ void launch_step_metal(const StepParams& p, cudaStream_t st)
     const int kz = step_kz(p);
     const int kzm = max(min(4, kz), kz / NLF_METAL_KZ_DIV);
     dim3 blk(BX, BY, 1);
-    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kzm - 1) / kzm);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, step_chunks(p, kz) * (kz / kzm));
     if (p.max_poles >= 1)
         k_step_metal<1><<<grd, blk, 0, st>>>(p, kz, kzm);
     else
@@ -1574,7 +1579,7 @@ void launch_step_pml(const StepParams& p, cudaStream_t st)
     static bool granted[64] = {};
     grant_smem(k_step_pml, smem, granted);
     dim3 blk(BX, BY, 1);
-    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, (p.nz + kz - 1) / kz);
+    dim3 grd((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, step_chunks(p, kz));
     k_step_pml<<<grd, blk, smem, st>>>(p, kz);
 }
 
