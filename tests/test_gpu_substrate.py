@@ -75,3 +75,34 @@ def test_slab_through_the_cpml_stays_bounded_on_the_gpu():
         e2.append(sum(float(np.sum(g.field(c).astype(np.float64) ** 2)) for c in ("Ex", "Ey", "Ez")))
     assert max(e2[-4:]) <= 1.5 * max(e2[:4]), e2
     g.close()
+
+
+@pytest.mark.parametrize("n3,bc,half", [
+    ((36, 20, 47), ("cpml", "cpml", "cpml"), (24, 14, 42)),
+    ((40, 16, 16), ("pec", "pec", "cpml"), (32, 8, 11)),
+], ids=["ragged_interior", "thinnest_grid"])
+def test_z_chunks_with_metal_through_the_z_cpml(n3, bc, half):
+    """The z chunks of the EM march with a CPML along z: the end chunks hold
+    the slab and one plane more, the interior ones kz planes (47 planes with
+    a 6-cell CPML: seven, then 8 + 8 + 8 + 8 + 1, then seven); the thinnest
+    grid a 6-cell CPML allows (16 planes) leaves a two-plane interior chunk.
+    A one-pole GNOR block that fills at least a quarter of the grid (so its
+    tiles update their sites inside the z march) runs through the z CPML
+    (local Drude there, sites of CPML tiles on the site list)."""
+    mat = W.drude_material(9.0, 0.07, beta=3.6e6, diff=1.9e-4, poles=[W.lorentz_pole()])
+    nx, ny, nz = n3
+    sh = {"kind": "box", "material": 1, "c": (nx, ny, nz), "half": half}
+    prob = {"shape": n3, "dx": 0.25e-9, "courant": 0.5, "pml": 6, "bc": bc, "eps_b": 1.0,
+            "materials": [mat], "shapes": [sh], "source": None, "monitors": None, "steps": 0}
+    g, o = start_pair(prob)
+    g.run(300)
+    g.sync()
+    o.step(300)
+    for vec, comps in VECTORS.items():
+        num = sum(np.sum((g.field(c).astype(np.float64) - o.array(c)) ** 2) for c in comps)
+        den = sum(np.sum(np.asarray(o.array(c)) ** 2) for c in comps)
+        assert den > 0, vec
+        assert np.sqrt(num / den) <= 1e-4, (vec, np.sqrt(num / den))
+    pz = np.asarray(o.array("Pz"))
+    assert np.max(np.abs(pz[:6])) > 1e-4 * np.max(np.abs(pz))       # the block is alive in the z CPML
+    g.close()
