@@ -138,6 +138,10 @@ FIELDS = {"Ex": 0, "Ey": 1, "Ez": 2, "Hx": 3, "Hy": 4, "Hz": 5, "Px": 6, "Py": 7
           "GDx_1": 21, "GDy_1": 22, "GDz_1": 23, "GDx_2": 24, "GDy_2": 25, "GDz_2": 26}
 
 
+class _SimView(np.ndarray):
+    """A view of memory that an oracle simulation owns (holds it alive)."""
+
+
 class Sim:
     """One oracle simulation built from a problem dict (see workloads.py)."""
 
@@ -236,11 +240,15 @@ class Sim:
 
     # -- state --------------------------------------------------------------
     def array(self, name: str) -> np.ndarray:
-        """Writable numpy view [nz, ny, nx] of an oracle array (SI units)."""
+        """Writable numpy view [nz, ny, nx] of an oracle array (SI units).
+        The view (and any array derived from it without a copy) keeps this
+        simulation, which owns the memory, alive."""
         p = lib().orc_array(self._h, FIELDS[name])
         if not p:
             raise KeyError(name)
-        return np.ctypeslib.as_array(p, shape=(self.ncell,)).reshape(self.shape3)
+        v = np.ctypeslib.as_array(p, shape=(self.ncell,)).reshape(self.shape3).view(_SimView)
+        v._owner = self
+        return v
 
     def material_map(self) -> np.ndarray:
         out = np.empty((3,) + self.shape3, dtype=np.uint8)
