@@ -155,13 +155,18 @@ typedef struct {
     long long pml_slab_cells;     /* sum over CPML axes of slab cells */
     long long dft_records;        /* flux-face samples (without the incident record) */
     double step_bytes;            /* algorithmic HBM bytes of one time step, the sum of the two below */
-    double step_kernel_bytes;     /* EM step kernel: 48 cells + 32 pml_slab_cells (E and H read
+    double step_kernel_bytes;     /* EM step kernels: 48 cells + 32 pml_slab_cells (E and H read
                                    * and written once, per slab cell and axis two psi_E read and
-                                   * written, two psi_H read and written) */
-    double metal_kernel_bytes;    /* material update: 21 material_sites (site entry and cell offset
-                                   * 8, id 1, E read and written 8, H 4) + 8 (2 + gnor) metal_sites
-                                   * (P_f, a_f and the GNOR history read and written)
-                                   * + 16 n_poles pole_sites */
+                                   * written, two psi_H read and written); when the metal tiles
+                                   * update their material sites inside the z march (a metal box
+                                   * of at least a quarter of the grid), also 1 per such site (its
+                                   * material id) + 8 (2 + gnor) + 16 n_poles per such plasmonic
+                                   * or pole site (P_f, a_f, the GNOR history, P_CP and a_CP read
+                                   * and written) */
+    double metal_kernel_bytes;    /* site-list material update (every material site, or with the
+                                   * fused form only those of CPML tiles): 21 per site (site entry
+                                   * and cell offset 8, id 1, E read and written 8, H 4) + 8 (2 +
+                                   * gnor) per plasmonic site + 16 n_poles per pole site */
     long long material_sites;     /* E-sites holding any material (entries of the site list) */
     double dt;                    /* s */
     int gnor, n_poles;
