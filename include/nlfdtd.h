@@ -347,7 +347,10 @@ int nlf_load_state(nlf_ctx* ctx, const void* host);
 /* Advance n independent contexts, steps[i] each, on `cuda_stream`: contexts
  * on the same DFT period advance together, every kernel of a time step
  * launched once over the concatenated work of all of them (one launch per
- * kernel per time step, replayed from a captured CUDA graph per DFT period),
+ * kernel per time step, replayed from a captured CUDA graph per DFT period);
+ * contexts left with the same number of steps short of a period advance
+ * together too (launched directly; the samples of that partial period stay
+ * buffered, as after nlf_run, until the next flush or nlf_get_spectra), and
  * the rest one context at a time.  status_out[i] receives each context's
  * status (NLF_OK or NLF_E_*).  All contexts must be configured; contexts with
  * a plane monitor are refused (NLF_E_ARG).  The paper has no counterpart

@@ -3,8 +3,9 @@
 // A batch step is one launch per kernel over the concatenated work of every
 // active instance: the step kernels take one block per (instance, tile, z
 // chunk) item of the joint work list (heaviest instances first) and run the
-// same tile code as the single-grid step; the material update walks the
-// joint material-site list grid-stride.  The monitor work of all instances is
+// same tile code as the single-grid step; the material sites and the TF/SF
+// items of all instances are one thread each over their joint lists.  The
+// monitor work of all instances is
 // batched the same way (one gather launch per sample, one phase and one
 // accumulation launch per block of samples).  The host captures a whole DFT
 // period of these launches in a CUDA graph.

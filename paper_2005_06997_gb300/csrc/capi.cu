@@ -32,7 +32,6 @@ void launch_step_metal(const StepParams& p, cudaStream_t st);
 bool step_has_pml(const StepParams& p);
 long long tfsf_items(const StepParams& p);
 void launch_tfsf(const StepParams& p, cudaStream_t st);
-void launch_tfsf_batch(const BatchStep& a, long long max_items, cudaStream_t st);
 void launch_metal(const StepParams& p, long long n_sites, cudaStream_t st);
 void launch_post(const StepParams& p, long long n_sites, cudaStream_t st);
 void launch_site_list(const uint8_t* mat, long long nb, uint32_t* sites, uint32_t* site_q, const SiteGeom& g,
@@ -50,7 +49,7 @@ void launch_watch(const float* E, long long nfloats, int* err, cudaStream_t st);
 void launch_density_out(const DensityParams& d, float* dst, cudaStream_t st);
 void launch_step_batch(const BatchStep& a, long long total_items, cudaStream_t st);
 void launch_step_batch_pml(const BatchStep& a, long long total_items, cudaStream_t st);
-void launch_metal_batch(const BatchStep& a, long long total_sites, cudaStream_t st);
+void launch_post_batch(const BatchStep& a, long long total_sites, long long total_tf, cudaStream_t st);
 void launch_gather_batch(const BatchDft& a, long long total_records, int slot, cudaStream_t st);
 void launch_flush_batch(const BatchDft& a, long long total_phase, long long total_chunks, int max_nf, int B,
                         int count, cudaStream_t st);
@@ -1073,7 +1072,7 @@ struct BatchPlan {
     char* dev = nullptr;              // descriptors (device)
     nlf::BatchStep bs{};
     nlf::BatchDft bd{};
-    long long items = 0, met_sites = 0, recs = 0, phases = 0, chunks = 0;
+    long long items = 0, met_sites = 0, tf_items = 0, recs = 0, phases = 0, chunks = 0;
     int max_nf = 0, K = 1, B = 8, U = 128;
     bool mon = false;
     int kz = 0;                       // z chunk used for every instance (0: per-instance heuristic)
@@ -1084,7 +1083,6 @@ struct BatchPlan {
     long long gnodes = 0;
     cudaStream_t cap = nullptr;
     bool any_pml = false;             // some instance has CPML tiles: second kernel on aux
-    long long tfsf_max = 0;           // largest TF/SF correction item count of an instance
     cudaStream_t aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     ~BatchPlan()
@@ -1109,9 +1107,9 @@ int plan_descriptors(BatchPlan* P, int kz)
     const int n = (int)P->ctxs.size();
     std::vector<nlf::StepParams> params(2 * n);
     std::vector<nlf::BatchInst> inst(n);
-    std::vector<long long> item_end(n), met_end(n), rec_end(n), ph_end(n), chunk_end(n);
+    std::vector<long long> item_end(n), met_end(n), tf_end(n), rec_end(n), ph_end(n), chunk_end(n);
     std::vector<nlf::BatchDftInst> dinst(n);
-    long long it = 0, ms = 0, rc = 0, ph = 0, ch = 0;
+    long long it = 0, ms = 0, tf = 0, rc = 0, ph = 0, ch = 0;
     P->max_nf = 0;
     for (int q = 0; q < n; ++q) {
         nlf_ctx* x = P->ctxs[q];
@@ -1133,6 +1131,8 @@ int plan_descriptors(BatchPlan* P, int kz)
         item_end[q] = it;
         if (x->has_metal) ms += x->n_msites;
         met_end[q] = ms;
+        tf += nlf::tfsf_items(x->sp[0]);
+        tf_end[q] = tf;
         if (P->mon) {
             nlf::BatchDftInst& d = dinst[q];
             d.d = x->dp;
@@ -1157,6 +1157,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     }
     P->items = it;
     P->met_sites = ms;
+    P->tf_items = tf;
     P->recs = rc;
     P->phases = ph;
     P->chunks = ch;
@@ -1170,6 +1171,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     const size_t o_inst = take(inst.size() * sizeof(nlf::BatchInst));
     const size_t o_item = take(n * sizeof(long long));
     const size_t o_met = take(n * sizeof(long long));
+    const size_t o_tf = take(n * sizeof(long long));
     const size_t o_dinst = take(dinst.size() * sizeof(nlf::BatchDftInst));
     const size_t o_rec = take(n * sizeof(long long));
     const size_t o_ph = take(n * sizeof(long long));
@@ -1183,6 +1185,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     memcpy(h.data() + o_inst, inst.data(), inst.size() * sizeof(nlf::BatchInst));
     memcpy(h.data() + o_item, item_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_met, met_end.data(), n * sizeof(long long));
+    memcpy(h.data() + o_tf, tf_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_dinst, dinst.data(), dinst.size() * sizeof(nlf::BatchDftInst));
     memcpy(h.data() + o_rec, rec_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_ph, ph_end.data(), n * sizeof(long long));
@@ -1192,6 +1195,7 @@ int plan_descriptors(BatchPlan* P, int kz)
     P->bs.inst = reinterpret_cast<const nlf::BatchInst*>(P->dev + o_inst);
     P->bs.item_end = reinterpret_cast<const long long*>(P->dev + o_item);
     P->bs.met_end = reinterpret_cast<const long long*>(P->dev + o_met);
+    P->bs.tf_end = reinterpret_cast<const long long*>(P->dev + o_tf);
     P->bs.n = n;
     P->bd.inst = reinterpret_cast<const nlf::BatchDftInst*>(P->dev + o_dinst);
     P->bd.rec_end = reinterpret_cast<const long long*>(P->dev + o_rec);
@@ -1202,13 +1206,15 @@ int plan_descriptors(BatchPlan* P, int kz)
     return NLF_OK;
 }
 
-// Launch one DFT period of batched work (step, gathers, flushes) on st;
-// returns the number of kernel launches.
-long long plan_launch(BatchPlan* P, cudaStream_t st)
+// Launch one DFT period of batched work (step, gathers, flushes) on st, or
+// its first `steps` time steps (steps < U: no flush, the samples stay in
+// their slots); returns the number of kernel launches.
+long long plan_launch(BatchPlan* P, cudaStream_t st, int steps = 0)
 {
     long long nodes = 0;
     int slot = 0;
-    for (int s = 0; s < P->U; ++s) {
+    const int S = steps > 0 ? steps : P->U;
+    for (int s = 0; s < S; ++s) {
         nlf::BatchStep bs = P->bs;
         bs.launch_par = s & 1;
         if (P->any_pml) {
@@ -1224,19 +1230,16 @@ long long plan_launch(BatchPlan* P, cudaStream_t st)
             nlf::launch_step_batch(bs, P->items, st);
             ++nodes;
         }
-        if (P->tfsf_max > 0) {
-            nlf::launch_tfsf_batch(bs, P->tfsf_max, st);
+        if (P->met_sites + P->tf_items > 0) {
+            // material sites and TF/SF items of every instance in one launch
+            nlf::launch_post_batch(bs, P->met_sites, P->tf_items, st);
             ++nodes;
         }
-        if (P->met_sites > 0) {
-            nlf::launch_metal_batch(bs, P->met_sites, st);
-            ++nodes;
-        }
-        if (s + 1 == P->U) {
+        if (s + 1 == S) {
             // the whole-grid non-finite watchdog of every instance
             for (size_t q = 0; q < P->ctxs.size(); ++q) {
                 nlf_ctx* x = P->ctxs[q];
-                const int cur = (P->par[q] + P->U) & 1;
+                const int cur = (P->par[q] + S) & 1;
                 nlf::launch_watch(at<float>(x, x->off_E[cur]), 3 * x->nfield, &at<Header>(x, x->off_hdr)->err, st);
                 ++nodes;
             }
@@ -1301,7 +1304,6 @@ BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
     P->U = act[0]->U;
     for (nlf_ctx* x : act) {
         if (nlf::step_has_pml(x->sp[0])) P->any_pml = true;
-        P->tfsf_max = std::max(P->tfsf_max, nlf::tfsf_items(x->sp[0]));
     }
     if (P->any_pml) {
         if (cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1365,6 +1367,27 @@ int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
     }
     P->uses += 1;
     for (nlf_ctx* x : P->ctxs) x->n += P->U;
+    return NLF_OK;
+}
+
+// Advance every instance of `act` (on a DFT period boundary, nothing
+// buffered) by `steps` < U time steps in batched launches, launched directly:
+// the samples of the partial period stay in their slots (cnt of each
+// context), to be accumulated by the next flush of the single-grid path.
+int batch_tail(const std::vector<nlf_ctx*>& act, int steps, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int rcode = NLF_OK;
+    BatchPlan* P = find_plan(act, &rcode);
+    if (!P) return rcode;
+    if (steps <= 0 || steps >= P->U) return NLF_E_ARG;
+    nlf_ctx* c = P->ctxs[0];
+    c->launches += plan_launch(P, st, steps);
+    CK(cudaGetLastError());
+    for (nlf_ctx* x : P->ctxs) {
+        x->n += steps;
+        if (P->mon) x->cnt = (steps / P->K) % P->B;   // a period of 2 K B steps flushes once within
+    }
     return NLF_OK;
 }
 
@@ -1954,6 +1977,27 @@ int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* stream, i
             rem[q] -= U;
         }
         if (r) break;
+    }
+    // members left with the same number of steps short of a period advance
+    // batched too, one group per remainder
+    std::vector<long long> tails;
+    for (int q : members)
+        if (rc[q] == NLF_OK && rem[q] > 0 && rem[q] < U &&
+            std::find(tails.begin(), tails.end(), rem[q]) == tails.end())
+            tails.push_back(rem[q]);
+    for (long long r : tails) {
+        std::vector<nlf_ctx*> act;
+        for (int q : members)
+            if (rc[q] == NLF_OK && rem[q] == r) act.push_back(ctxs[q]);
+        if (act.size() < 2) continue;
+        const int e = batch_tail(act, (int)r, st);
+        for (int q : members)
+            if (rc[q] == NLF_OK && rem[q] == r) {
+                if (e)
+                    rc[q] = e;
+                else
+                    rem[q] = 0;
+            }
     }
     for (int q : batchable) {
         if (rc[q] == NLF_OK && rem[q] > 0) rc[q] = nlf_run(ctxs[q], rem[q], stream);

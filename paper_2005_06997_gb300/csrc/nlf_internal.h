@@ -327,7 +327,8 @@ struct BatchStep {
     const StepParams* params;   // [2 n]
     const BatchInst* inst;      // [n]
     const long long* item_end;  // [n] inclusive prefix sums of work items
-    const long long* met_end;   // [n] inclusive prefix sums of metal-box sites (3 per cell)
+    const long long* met_end;   // [n] inclusive prefix sums of material sites
+    const long long* tf_end;    // [n] inclusive prefix sums of TF/SF correction items
     int n;
     int launch_par;
 };
