@@ -193,6 +193,42 @@ CONFIGS = {
 }
 
 
+def curl_pulse(shape3, center, width):
+    """A divergence-free initial E on the Yee lattice: the discrete curl of
+    A z-hat, A a separable Gaussian (centre and 1/e half-widths in cells, x,
+    y, z) held at the (i+1/2, j+1/2, k) points, so that E_x[k, j, i] = A[k,
+    j, i] - A[k, j-1, i] and E_y[k, j, i] = A[k, j, i-1] - A[k, j, i]; the
+    tangential E on the walls is zero.  Returns (E_x, E_y) as [nz][ny][nx]
+    float32 arrays (unit peak of A)."""
+    nz, ny, nx = shape3
+    gx = np.exp(-(((np.arange(nx) + 0.5 - center[0]) / width[0]) ** 2)).astype(np.float32)
+    gy = np.exp(-(((np.arange(ny) + 0.5 - center[1]) / width[1]) ** 2)).astype(np.float32)
+    gz = np.exp(-(((np.arange(nz) - center[2]) / width[2]) ** 2)).astype(np.float32)
+    dy = np.zeros(ny, np.float32)
+    dy[1:] = gy[1:] - gy[:-1]
+    dx = np.zeros(nx, np.float32)
+    dx[1:] = gx[:-1] - gx[1:]
+    gz0 = gz.copy()
+    gz0[0] = 0.0
+    ex = gz0[:, None, None] * dy[None, :, None] * gx[None, None, :]
+    ey = gz0[:, None, None] * gy[None, :, None] * dx[None, None, :]
+    return ex, ey
+
+
+def pulse_run(name):
+    """The full-size field runs: a configured workload's grid, materials and
+    particle without the source and monitors, started from a curl_pulse
+    centred on the particle, for a fixed number of steps.  Returns (prob,
+    (E_x, E_y), steps)."""
+    base, steps, width = {"cube_tips_au_gnor_512_pulse": ("cube_tips_au_gnor_512", 200, 24.0)}[name]
+    prob = CONFIGS[base]()
+    prob["source"] = None
+    prob["monitors"] = None
+    prob["steps"] = steps
+    nx, ny, nz = prob["shape"]
+    return prob, curl_pulse((nz, ny, nx), (nx / 2, ny / 2, nz / 2), (width,) * 3), steps
+
+
 def small_sphere(n=36, radius_cells=5.0, pml=6, material=None, steps=200, band_ev=(1.0, 9.0), nf=16,
                  K=4, center_offset_half=(1, 0, -1), dx=0.5e-9, t0_tau=2.5):
     """A small test problem that spans several tiles and has ragged edges; the

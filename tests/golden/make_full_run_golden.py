@@ -2,6 +2,7 @@
 """Write the FP64 oracle's results for a full-length run of a named workload.
 
     python tests/golden/make_full_run_golden.py sphere_au_gnor_r10nm_224
+    python tests/golden/make_full_run_golden.py cube_tips_au_gnor_512_pulse
 
 Calls only ``oracle/`` (and the seeded problem descriptions of
 ``paper_2005_06997_gb300.workloads``, which hold no method arithmetic).  The
@@ -22,6 +23,10 @@ of time steps).  Stored in ``tests/golden/full_run_<workload>.npz``:
 
 The samples are drawn with numpy.random.default_rng(20050697) from sizes
 alone, so the GPU test draws the same sites without running the oracle.
+
+A pulse run (workloads.pulse_run: a workload's grid and particle without
+source and monitors, started from a divergence-free pulse) stores the field
+entries only; its sample box is the particle's bounding box.
 """
 from __future__ import annotations
 
@@ -74,12 +79,27 @@ def particle_box(prob):
     return tuple(mo["abs_lo"]), tuple(mo["abs_hi"])
 
 
+def metal_box(vox):
+    """Inclusive cell bounds (x, y, z) of every E-site that holds a material."""
+    any_m = (vox[0] != 0) | (vox[1] != 0) | (vox[2] != 0)
+    ks, js, is_ = (np.flatnonzero(any_m.any(axis=a)) for a in ((1, 2), (0, 2), (0, 1)))
+    return (int(is_[0]), int(js[0]), int(ks[0])), (int(is_[-1]), int(js[-1]), int(ks[-1]))
+
+
 def main():
     name = sys.argv[1] if len(sys.argv) > 1 else "sphere_au_gnor_r10nm_224"
-    prob = W.CONFIGS[name]()
-    steps = int(prob["steps"])
+    pulse = name not in W.CONFIGS
+    if pulse:
+        prob, (ex, ey), steps = W.pulse_run(name)
+    else:
+        prob = W.CONFIGS[name]()
+        steps = int(prob["steps"])
     t0 = time.time()
     s = oracle.Sim(prob)
+    if pulse:
+        s.array("Ex")[...] = ex
+        s.array("Ey")[...] = ey
+        del ex, ey
     done = 0
     chunk = 256
     while done < steps:
@@ -87,7 +107,7 @@ def main():
         s.step(k)
         done += k
         print("%s: %d / %d steps, %.0f s" % (name, done, steps, time.time() - t0), flush=True)
-    spec = s.spectra()
+    spec = None if pulse else s.spectra()
     vox = s.material_map()
     metal_flat = []
     for c in range(3):
@@ -96,19 +116,20 @@ def main():
             if m.get("wp", 0.0) > 0.0:
                 plas |= vox[c].reshape(-1) == q + 1
         metal_flat.append(np.flatnonzero(plas))
-    lo, hi = particle_box(prob)
-    smp = sample_sites(s.shape3, lo, hi, metal_flat, s.nrec)
-    out = {"ext": spec["ext"], "abs": spec["abs"], "sca": spec["sca"], "inc": spec["inc"]}
+    lo, hi = metal_box(vox) if pulse else particle_box(prob)
+    smp = sample_sites(s.shape3, lo, hi, metal_flat, 64 if pulse else s.nrec)
+    out = {} if pulse else {"ext": spec["ext"], "abs": spec["abs"], "sca": spec["sca"], "inc": spec["inc"]}
     for fname in ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Px", "Py", "Pz"):
         a = np.asarray(s.array(fname), dtype=np.float64).reshape(-1)
         out["sumsq_" + fname] = np.array(float(np.sum(a * a)))
         out["idx_" + fname] = smp[fname]
         out["val_" + fname] = a[smp[fname]]
-    aE, aH = s.dft()
-    rows = np.concatenate([smp["rec"], [s.nrec]]).astype(np.int32)
-    out["rec_idx"] = rows
-    out["dftE"] = aE[rows]
-    out["dftH"] = aH[rows]
+    if not pulse:
+        aE, aH = s.dft()
+        rows = np.concatenate([smp["rec"], [s.nrec]]).astype(np.int32)
+        out["rec_idx"] = rows
+        out["dftE"] = aE[rows]
+        out["dftH"] = aH[rows]
     try:
         rev = subprocess.run(["git", "-C", ROOT, "rev-parse", "--short", "HEAD"], capture_output=True,
                              text=True).stdout.strip()

@@ -62,3 +62,51 @@ def test_full_length_run_matches_stored_oracle_run(name):
     assert not bad, (bad, errs)
     assert int(np.argmax(spec["ext"])) == int(np.argmax(g["ext"]))
     s.close()
+
+
+PULSE_RUNS = ["cube_tips_au_gnor_512_pulse"]
+ETA0 = 376.730313668
+
+
+@pytest.mark.parametrize("name", PULSE_RUNS)
+def test_full_size_pulse_run_matches_stored_oracle_run(name):
+    """The full 512^3 grid of the benchmark's cube with tips (12-cell CPML,
+    GNOR with a Lorentz pole, metal box a quarter of the grid, so the metal
+    tiles update their sites inside the z march) without source and monitors,
+    started from a divergence-free pulse centred on the particle
+    (workloads.pulse_run), against the oracle's stored run of the same
+    problem.  E and P_f over the stored sites and as whole-grid norms within
+    1e-4; H in the field's norm (eta0 H against E and eta0 H together), the
+    near field of the particle holding little H."""
+    path = os.path.join(GOLDEN, "full_run_%s.npz" % name)
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle run for %s" % name)
+    g = np.load(path)
+    prob, (ex, ey), steps = W.pulse_run(name)
+    s = nlfdtd.Solver(prob)
+    s.set_field("Ex", ex)
+    s.set_field("Ey", ey)
+    del ex, ey
+    s.run(steps)
+    s.sync()
+    assert s.n == steps
+    d2, r2, n_got, n_ref = {}, {}, {}, {}
+    for vec in ("E", "H", "P"):
+        d2[vec] = r2[vec] = n_got[vec] = n_ref[vec] = 0.0
+        for c in "xyz":
+            f = vec + c
+            a = s.field(f).astype(np.float64).reshape(-1)
+            ref = g["val_" + f]
+            d2[vec] += float(np.sum((a[g["idx_" + f]] - ref) ** 2))
+            r2[vec] += float(np.sum(ref ** 2))
+            n_got[vec] += float(np.sum(a * a))
+            n_ref[vec] += float(g["sumsq_" + f])
+    errs = {"samples_E": np.sqrt(d2["E"] / r2["E"]), "samples_P": np.sqrt(d2["P"] / r2["P"]),
+            "samples_H": ETA0 * np.sqrt(d2["H"] / (r2["E"] + ETA0 ** 2 * r2["H"]))}
+    for vec in ("E", "P"):
+        errs["norm_" + vec] = abs(np.sqrt(n_got[vec]) - np.sqrt(n_ref[vec])) / np.sqrt(n_ref[vec])
+    errs["norm_H"] = ETA0 * abs(np.sqrt(n_got["H"]) - np.sqrt(n_ref["H"])) / np.sqrt(n_ref["E"] + ETA0 ** 2 * n_ref["H"])
+    assert all(v > 0 for v in r2.values()), r2
+    bad = {k: v for k, v in errs.items() if not v <= 1e-4}
+    assert not bad, (bad, errs)
+    s.close()
