@@ -158,7 +158,7 @@ __global__ void k_dft_gather(const DftParams d, const float* __restrict__ E, con
                              const long long* __restrict__ step, int* err)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r > d.nrec) return;
+    if (r > d.nrec || !NLF_CTX(d)) return;
     float e, h;
     if (r < d.nrec) {
         const uint32_t oe = d.rec_e[r], o = d.rec_h[r], hs = d.rec_hs[r];
@@ -182,7 +182,7 @@ __global__ void k_dft_gather(const DftParams d, const float* __restrict__ E, con
 __global__ void k_dft_phase(const DftParams d, int count)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= d.B * d.nf) return;
+    if (t >= d.B * d.nf || !NLF_CTX(d)) return;
     const int s = t / d.nf, f = t - s * d.nf;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (s < count) {

@@ -43,6 +43,7 @@ __global__ void k_gather_batch(const BatchDft a, int slot)
     const long long r = w - (q > 0 ? a.rec_end[q - 1] : 0);
     const int cur = I.base_par ^ a.cur_par;
     const DftParams& d = I.d;
+    if (!NLF_CTX(d)) return;
     float e, h;
     if (r < d.nrec) {
         const uint32_t oe = d.rec_e[r], o = d.rec_h[r], hs = d.rec_hs[r];
@@ -68,6 +69,7 @@ __global__ void k_phase_batch(const BatchDft a, int count)
     if (w >= total) return;
     const int q = find_inst(a.ph_end, a.n, w);
     const DftParams& d = a.inst[q].d;
+    if (!NLF_CTX(d)) return;
     const long long t = w - (q > 0 ? a.ph_end[q - 1] : 0);
     const int s = (int)(t / d.nf), f = (int)(t - (long long)s * d.nf);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -10,14 +10,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <unordered_set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -68,6 +71,7 @@ struct Header {            // first bytes of the state buffer
     int cnt;               // pending DFT samples (host mirror, written before a save)
     long long n;           // time index (host mirror, written before a save)
     nlf::BoundsRecord chk; // first out-of-bounds access of the bounds-checked build
+    long long ctx_id;      // the id of the context that owns this state
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -75,6 +79,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 }  // namespace
 
 struct nlf_ctx {
+    long long id = 0;               // unique per context of the process (also in the state's header)
     nlf_grid g{};
     double dt = 0, c0 = 0, eta0 = 0;
     long long ncell = 0;
@@ -652,6 +657,8 @@ void fill_params(nlf_ctx* c)
         p.step1 = &h->step[w];
         p.err = &h->err;
         p.chk = &h->chk;
+        p.hdr_id = &h->ctx_id;
+        p.ctx_id = c->id;
         p.nfield = c->nfield;
         for (int a = 0; a < 3; ++a) p.psi_n[a] = c->pml_slab[a];
         p.nbb = c->nbb;
@@ -699,6 +706,8 @@ void fill_params(nlf_ctx* c)
         d.nfield3 = 3 * c->nfield;
         d.err = &at<Header>(c, c->off_hdr)->err;
         d.chk = &at<Header>(c, c->off_hdr)->chk;
+        d.hdr_id = &at<Header>(c, c->off_hdr)->ctx_id;
+        d.ctx_id = c->id;
     }
 }
 
@@ -715,6 +724,7 @@ int initialise(nlf_ctx* c, cudaStream_t st)
         return NLF_OK;
     };
     int rc;
+    if ((rc = put(c->off_hdr + offsetof(Header, ctx_id), &c->id, sizeof c->id))) return rc;
     if ((rc = encode_maps(c))) return rc;
     if ((rc = put(c->off_tmap, c->tmaps, sizeof c->tmaps))) return rc;
     for (int a = 0; a < 3; ++a) {
@@ -1098,6 +1108,19 @@ struct BatchPlan {
 
 std::mutex g_batch_mu;
 std::vector<std::unique_ptr<BatchPlan>> g_plans;
+// Contexts created and not yet destroyed (guarded by g_batch_mu): a batched
+// plan is launched only while every context it holds is among them.
+std::unordered_set<const nlf_ctx*> g_live;
+
+// NLF_OK if every context of plan P is alive and has its state, else the
+// error recorded on the plan's first context.
+int plan_alive(BatchPlan* P)
+{
+    for (nlf_ctx* x : P->ctxs)
+        if (!g_live.count(x) || !x->ready || !x->base)
+            return fail(P->ctxs[0], NLF_E_STATE, "batched plan holds a context that was released or not initialised");
+    return NLF_OK;
+}
 const int kTuneKz[] = {8, 16, 32};
 
 // Build the device descriptors of a plan for z chunk kz (0: heuristic).
@@ -1331,6 +1354,7 @@ int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
     int rcode = NLF_OK;
     BatchPlan* P = find_plan(act, &rcode);
     if (!P) return rcode;
+    if ((rcode = plan_alive(P))) return rcode;
     nlf_ctx* c = P->ctxs[0];
     const int ncand = (int)(sizeof(kTuneKz) / sizeof(kTuneKz[0]));
     if (g_kz_best == 0) {
@@ -1380,6 +1404,7 @@ int batch_tail(const std::vector<nlf_ctx*>& act, int steps, cudaStream_t st)
     int rcode = NLF_OK;
     BatchPlan* P = find_plan(act, &rcode);
     if (!P) return rcode;
+    if ((rcode = plan_alive(P))) return rcode;
     if (steps <= 0 || steps >= P->U) return NLF_E_ARG;
     nlf_ctx* c = P->ctxs[0];
     c->launches += plan_launch(P, st, steps);
@@ -1391,9 +1416,16 @@ int batch_tail(const std::vector<nlf_ctx*>& act, int steps, cudaStream_t st)
     return NLF_OK;
 }
 
+void register_ctx(const nlf_ctx* x)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_live.insert(x);
+}
+
 void drop_plans(const nlf_ctx* x)
 {
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_live.erase(x);
     for (size_t q = 0; q < g_plans.size();) {
         if (std::find(g_plans[q]->ctxs.begin(), g_plans[q]->ctxs.end(), x) != g_plans[q]->ctxs.end())
             g_plans.erase(g_plans.begin() + q);
@@ -1422,7 +1454,9 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out)
         const int n = a == 0 ? g.nx : a == 1 ? g.ny : g.nz;
         if (g.boundary[a] == NLF_BC_CPML && (g.pml_cells < 1 || 2 * g.pml_cells + 4 > n)) return NLF_E_ARG;
     }
+    static std::atomic<long long> next_id{0};
     nlf_ctx* c = new nlf_ctx();
+    c->id = ++next_id;
     c->g = g;
     c->c0 = 1.0 / std::sqrt(kEps0 * kMu0);
     c->eta0 = std::sqrt(kMu0 / kEps0);
@@ -1430,6 +1464,7 @@ int nlf_create(const nlf_grid* grid, nlf_ctx** out)
     c->ncell = (long long)g.nx * g.ny * g.nz;
     c->px = (g.nx + 7) & ~7;
     c->nfield = (long long)c->px * g.ny * g.nz;
+    register_ctx(c);
     *out = c;
     return NLF_OK;
 }
@@ -1698,6 +1733,9 @@ int nlf_sync(nlf_ctx* c, int timeout_ms)
     }
     Header h{};
     CK(cudaMemcpy(&h, c->base + c->off_hdr, sizeof h, cudaMemcpyDeviceToHost));
+    if (h.err & 8 && h.chk.code == 30)
+        return fail(c, NLF_E_CUDA, "context check: parameters made for context %lld ran on the state of context %lld "
+                    "(this context: %lld; %d launches' work skipped)", h.chk.lim, h.chk.idx, c->id, h.chk.hits);
     if (h.err & 8)
         return fail(c, NLF_E_CUDA, "bounds check: access site %d index %lld outside [0, %lld) (%d accesses skipped)",
                     h.chk.code, h.chk.idx, h.chk.lim, h.chk.hits);
@@ -1918,8 +1956,10 @@ int nlf_load_state(nlf_ctx* c, const void* host)
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpy(c->base, host, c->bytes, cudaMemcpyHostToDevice));
-    // the tensor maps hold this buffer's addresses, not the saved state's
+    // the tensor maps hold this buffer's addresses, not the saved state's,
+    // and the header this context's id
     CK(cudaMemcpy(c->base + c->off_tmap, c->tmaps, sizeof c->tmaps, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->base + c->off_hdr + offsetof(Header, ctx_id), &c->id, sizeof c->id, cudaMemcpyHostToDevice));
     Header h{};
     memcpy(&h, host, sizeof h);
     c->n = h.n;

@@ -95,6 +95,7 @@ template <int B, int RCH>
 __device__ __forceinline__ void accum_block(const DftParams& d, long long rb, int nchunk, int f0,
                                             AccShared<B, RCH>& sm)
 {
+    if (!NLF_CTX(d)) return;        // (uniform over the block)
     const int t = threadIdx.x;
     for (int q = t; q < B * ACC_NT; q += blockDim.x) {
         const int s = q / ACC_NT, u = q - s * ACC_NT;

@@ -63,8 +63,26 @@ __device__ __forceinline__ bool nlf_in_bounds(int* err, BoundsRecord* rec, int c
     return false;
 }
 #define NLF_IN(P, CODE, IDX, LIM) ::nlf::nlf_in_bounds((P).err, (P).chk, (CODE), (long long)(IDX), (long long)(LIM))
+// The state these parameters point into still belongs to the context they
+// were made for (its header holds that context's id): a mismatch (a plan, a
+// graph or a parameter block that outlived its context, or whose memory went
+// to another one) is recorded as access site 30 and the work is skipped.
+__device__ __forceinline__ bool nlf_ctx_ok(int* err, BoundsRecord* rec, const long long* hdr_id, long long ctx_id)
+{
+    const long long held = *hdr_id;
+    if (held == ctx_id) return true;
+    if (err) atomicOr(err, 8);
+    if (rec && atomicCAS(&rec->code, 0, 30) == 0) {
+        rec->idx = held;
+        rec->lim = ctx_id;
+    }
+    if (rec) atomicAdd(&rec->hits, 1);
+    return false;
+}
+#define NLF_CTX(P) ::nlf::nlf_ctx_ok((P).err, (P).chk, (P).hdr_id, (P).ctx_id)
 #else
 #define NLF_IN(P, CODE, IDX, LIM) true
+#define NLF_CTX(P) true
 #endif
 
 // The CPML slab axes that the cell box [lo, hi] (inclusive) reaches, bit a
@@ -245,6 +263,8 @@ struct StepParams {
     long long nbb;
     int ntiles_xy;
     BoundsRecord* chk;
+    const long long* hdr_id;    // the context id in the state's header, and the id these parameters
+    long long ctx_id;           // were made for (compared by the bounds-checked build's kernels)
 };
 
 struct VoxParams {
@@ -314,6 +334,8 @@ struct DftParams {
     long long nfield3;          // floats of the three components of E (and of H): bounds-checked build
     int* err;
     BoundsRecord* chk;
+    const long long* hdr_id;    // as in StepParams
+    long long ctx_id;
 };
 
 // Batched stepping: instance q uses params[2 q + (base_par ^ launch parity)].

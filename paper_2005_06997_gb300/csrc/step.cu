@@ -295,6 +295,7 @@ __device__ __forceinline__ void metal_site(const StepParams& p, uint32_t b, uint
 // set for a site of a CPML cell, box offset below; cell offset q).
 __device__ __forceinline__ void metal_entry(const StepParams& p, long long t)
 {
+    if (!NLF_CTX(p)) return;
     const uint32_t e = __ldg(p.sites + t), q = __ldg(p.site_q + t);
     const uint32_t c = e >> 30, b = e & NLF_SITE_OFFSET_MASK;
     if (e & NLF_SITE_IN_CPML) {
@@ -1158,6 +1159,7 @@ __device__ __forceinline__ bool metal_subchunk(const StepParams& p, int bx, int 
 template <int KIND, int MP, class SM>
 __device__ __forceinline__ void step_tile_of(const StepParams& p, int bx, int by, int bz, int kz, SM& sm, int kzm = 0)
 {
+    if (!NLF_CTX(p)) return;        // (uniform over the block)
     const int x0 = bx * BX, y0 = by * BY;
     int k0 = 0, k1 = 0, c0 = 0, c1 = 0;
     if constexpr (KIND == TILE_MET) {
@@ -1299,6 +1301,7 @@ __host__ __device__ __forceinline__ long long tfsf_count(const StepParams& p)
 
 __device__ __forceinline__ void tfsf_item(const StepParams& p, long long t)
 {
+    if (!NLF_CTX(p)) return;
     const int l0 = p.tf_lo[0], h0 = p.tf_hi[0], l1 = p.tf_lo[1], h1 = p.tf_hi[1], l2 = p.tf_lo[2],
               h2 = p.tf_hi[2];
     const int nx = h0 - l0, ny = h1 - l1 + 1;
