@@ -27,9 +27,11 @@ GNOR sphere with a Lorentz pole (8000 steps) is reported beside it under
            byte count of one time step (fields, hydrodynamic state, CPML,
            material ids, running DFT)
   cpu_baseline - the FP64 CPU oracle on a bounded sample of the same workload
-  serving - solves/s and p50/p99 latency of the seeded 256-request stream,
-           continuous batching against one grid at a time, at the stated
-           20 req/s and at 0.7 of the plain form's capacity
+  serving - (with --serving N) solves/s and p50/p99 latency of the seeded
+           256-request stream, continuous batching against one grid at a
+           time, at the stated 20 req/s and at 0.7 of the plain form's
+           capacity; off by default while an illegal memory access that its
+           full run has met is unexplained
   batched - the 64-instance batched configuration (uneven 40^3..128^3 grids,
            4000 time steps each) advanced together by nlf_batch_run, against
            the same solves run one grid per launch sequence (wall time)
