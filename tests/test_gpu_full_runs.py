@@ -58,6 +58,7 @@ def test_full_length_run_matches_stored_oracle_run(name):
     inc = g["inc"]
     m = inc >= 1e-3 * inc.max()
     errs["sigma_ext"] = float(np.max(np.abs(spec["ext"][m] - g["ext"][m])) / np.max(np.abs(g["ext"][m])))
+    print(name, "errors", errs)
     bad = {k: v for k, v in errs.items() if not (v <= (1e-3 if k == "sigma_ext" else 1e-4))}
     assert not bad, (bad, errs)
     assert int(np.argmax(spec["ext"])) == int(np.argmax(g["ext"]))
@@ -107,6 +108,7 @@ def test_full_size_pulse_run_matches_stored_oracle_run(name):
         errs["norm_" + vec] = abs(np.sqrt(n_got[vec]) - np.sqrt(n_ref[vec])) / np.sqrt(n_ref[vec])
     errs["norm_H"] = ETA0 * abs(np.sqrt(n_got["H"]) - np.sqrt(n_ref["H"])) / np.sqrt(n_ref["E"] + ETA0 ** 2 * n_ref["H"])
     assert all(v > 0 for v in r2.values()), r2
+    print(name, "errors", errs)
     bad = {k: v for k, v in errs.items() if not v <= 1e-4}
     assert not bad, (bad, errs)
     s.close()
