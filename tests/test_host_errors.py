@@ -165,3 +165,49 @@ def test_plane_monitor_outside_the_grid_is_refused(L):
     pm = nlfdtd.nlf_plane_monitor(2, 3, 1, om.ctypes.data_as(C.POINTER(C.c_double)), 4)
     assert L.nlf_set_plane_monitor(h, C.byref(pm)) == 0
     L.nlf_destroy(h)
+
+
+def _grid(n3, pml=6, bc=("cpml",) * 3, courant=0.5):
+    g = nlfdtd.nlf_grid()
+    g.nx, g.ny, g.nz = n3
+    g.dx, g.courant, g.pml_cells, g.eps_background = 1e-9, courant, pml, 1.0
+    for a in range(3):
+        g.boundary[a] = 1 if bc[a] == "cpml" else 0
+    return g
+
+
+def _create(L, g):
+    h = C.c_void_p()
+    rc = L.nlf_create(C.byref(g), C.byref(h))
+    if rc == 0:
+        L.nlf_destroy(h)
+    return rc
+
+
+def test_grid_limits(L):
+    """Edge cases of the grid: the smallest grid (8 cells on every axis), the
+    thinnest axis a CPML of L cells allows (2 L + 4 cells), the largest grid
+    whose 32-bit offsets of three components fit (3 px ny nz < 2^32, px = nx
+    rounded up to 8), and one cell past each limit."""
+    assert _create(L, _grid((8, 8, 8), bc=("pec",) * 3)) == 0
+    assert _create(L, _grid((7, 8, 8), bc=("pec",) * 3)) == E_ARG
+    assert _create(L, _grid((16, 16, 16), pml=6)) == 0
+    assert _create(L, _grid((15, 16, 16), pml=6)) == E_ARG
+    assert _create(L, _grid((16, 16, 16), pml=0)) == E_ARG            # a CPML needs at least one cell
+    # 3 px ny nz < 2^32: with px = ny = 1024, nz = 1365 fits, 1366 does not
+    assert 3 * 1024 * 1024 * 1365 < 2 ** 32 <= 3 * 1024 * 1024 * 1366
+    assert _create(L, _grid((1024, 1024, 1365))) == 0
+    assert _create(L, _grid((1024, 1024, 1366))) == E_ARG
+    assert _create(L, _grid((1017, 1024, 1365))) == 0                  # px = 1024 as well
+    assert _create(L, _grid((32, 32, 32), courant=0.5774)) == E_CFL     # S above 1/sqrt(3)
+
+
+def test_batch_run_arguments_are_checked_on_the_host(L):
+    """nlf_batch_run refuses a batch larger than NLF_MAX_BATCH (256) or
+    without step counts before touching any context or the device."""
+    hs = (C.c_void_p * 257)()
+    steps = (C.c_longlong * 257)()
+    status = (C.c_int * 257)()
+    assert L.nlf_batch_run(hs, 257, steps, None, status) == E_ARG
+    assert L.nlf_batch_run(hs, 1, None, None, status) == E_ARG
+    assert L.nlf_batch_run(hs, -1, steps, None, status) == E_ARG
