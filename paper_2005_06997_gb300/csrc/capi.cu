@@ -565,6 +565,14 @@ void fill_params(nlf_ctx* c)
         p.px = c->px;
         p.tmE = c->base + c->off_tmap + (size_t)r * sizeof(CUtensorMap);
         p.tmH = c->base + c->off_tmap + (size_t)(2 + r) * sizeof(CUtensorMap);
+        static_assert(sizeof(nlf::TensorMapBytes) == sizeof(CUtensorMap), "tensor map size");
+        memcpy(&p.mapE, &c->tmaps[r], sizeof(CUtensorMap));
+        memcpy(&p.mapH, &c->tmaps[2 + r], sizeof(CUtensorMap));
+#ifdef NLF_TMAP_GLOBAL
+        p.map_in_params = 0;            // build option: the maps from the state in global memory
+#else
+        p.map_in_params = 1;
+#endif
         p.ny = c->g.ny;
         p.nz = c->g.nz;
         p.S = (float)c->g.courant;
@@ -1138,6 +1146,10 @@ int plan_descriptors(BatchPlan* P, int kz)
         nlf_ctx* x = P->ctxs[q];
         params[2 * q] = x->sp[0];
         params[2 * q + 1] = x->sp[1];
+        // a block stages its instance's parameters in shared memory, where a
+        // tensor map cannot be read from: the maps come from the state
+        params[2 * q].map_in_params = 0;
+        params[2 * q + 1].map_in_params = 0;
         for (int g2 = 0; g2 < 2 && x->has_metal; ++g2) {
             // batched steps update every material site from the full list
             params[2 * q + g2].fuse_metal = 0;

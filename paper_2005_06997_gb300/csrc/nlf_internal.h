@@ -185,6 +185,11 @@ struct Shape {
     int side, tip_base, tip_height, tip_radius, tip_center, tip_cut;
 };
 
+// The 128 opaque bytes of a CUDA tensor map (the layout of CUtensorMap).
+struct alignas(64) TensorMapBytes {
+    unsigned long long w[16];
+};
+
 // Everything the fused time step needs.  Pointers are device pointers.
 struct StepParams {
     int nx, ny, nz;
@@ -265,6 +270,12 @@ struct StepParams {
     BoundsRecord* chk;
     const long long* hdr_id;    // the context id in the state's header, and the id these parameters
     long long ctx_id;           // were made for (compared by the bounds-checked build's kernels)
+    // copies of the maps tmE and tmH point to; with map_in_params set (the
+    // single-grid kernels, whose parameter block is a grid constant) the
+    // copies read them from the kernel parameter, else (a block's copy of
+    // the parameters in shared memory, the batched kernels) from tmE / tmH
+    TensorMapBytes mapE, mapH;
+    int map_in_params;
 };
 
 struct VoxParams {

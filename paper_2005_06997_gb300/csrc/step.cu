@@ -668,14 +668,16 @@ struct TmaRing {
         // (TMA_TEST_EXTRA: 0 except in the stall test build, which poisons
         // the first E stage of the background kernel's blocks)
         const unsigned extra = (TMA_TEST_EXTRA && !SM::kPoisonFree && pl == k0 - 1) ? TMA_TEST_EXTRA : 0u;
-        tma_plane(sm.sE[q], p.tmE, x0 - 4, y0 - 1, pl, &sm.barE[q], TMA_E_FLOATS * 4 + extra);
+        tma_plane(sm.sE[q], p.map_in_params ? static_cast<const void*>(&p.mapE) : p.tmE, x0 - 4, y0 - 1, pl,
+                  &sm.barE[q], TMA_E_FLOATS * 4 + extra);
         pendE |= 1u << q;
         parE = (parE & ~(1u << q)) | (epar(pl) << q);
     }
     __device__ void issue_h(int pl)
     {
         const int q = hslot(pl);
-        tma_plane(sm.sHo[q], p.tmH, x0 - 4, y0 - 1, pl, &sm.barH[q], TMA_H_FLOATS * 4);
+        tma_plane(sm.sHo[q], p.map_in_params ? static_cast<const void*>(&p.mapH) : p.tmH, x0 - 4, y0 - 1, pl,
+                  &sm.barH[q], TMA_H_FLOATS * 4);
         pendH |= 1u << q;
         parH = (parH & ~(1u << q)) | (hpar(pl) << q);
     }
@@ -822,9 +824,12 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         for (int q = 0; q < NE; ++q) mbar_init(&sm.barE[q]);
         for (int q = 0; q < NH; ++q) mbar_init(&sm.barH[q]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        // the tensor maps were written to device memory by a copy, not by this proxy
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmE) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmH) : "memory");
+        // maps read from the state were written to device memory by a copy,
+        // not by this proxy (maps in the kernel parameter need no fence)
+        if (!p.map_in_params) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmE) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmH) : "memory");
+        }
     }
     __syncthreads();
     // E planes k0-1 .. k0+NE-2 and H planes k0 .. k0+NH-1 (E is needed up to plane k1, H up to k1-1)
@@ -1204,7 +1209,7 @@ using SharedMET = TileSharedTMA<NE_STAGE, NH_STAGE, false, true>;
 static_assert(PML_BLOCKS * (sizeof(SharedPML) + 128 + 1024) <= 228 * 1024, "CPML tile blocks do not fit an SM");
 static_assert(sizeof(SharedMET) <= 48 * 1024, "metal tile shared memory exceeds the static limit");
 
-__global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
+__global__ void __launch_bounds__(BX * BY, 5) k_step(const __grid_constant__ StepParams p, int kz)
 {
     __shared__ SharedBG sm;
     step_tile_of<TILE_BG, -1>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm);
@@ -1220,7 +1225,8 @@ __global__ void __launch_bounds__(BX * BY, 5) k_step(const StepParams p, int kz)
 #define NLF_METAL_KZ_DIV 2
 #endif
 template <int MP>
-__global__ void __launch_bounds__(BX * BY, NLF_METAL_BLOCKS) k_step_metal(const StepParams p, int kz, int kzm)
+__global__ void __launch_bounds__(BX * BY, NLF_METAL_BLOCKS) k_step_metal(const __grid_constant__ StepParams p, int kz,
+                                                                          int kzm)
 {
     __shared__ SharedMET sm;
     step_tile_of<TILE_MET, MP>(p, blockIdx.x, blockIdx.y, blockIdx.z, kz, sm, kzm);
@@ -1228,7 +1234,7 @@ __global__ void __launch_bounds__(BX * BY, NLF_METAL_BLOCKS) k_step_metal(const 
 
 // CPML tiles: TMA rings plus the psi staging area exceed the 48 KB of static
 // shared memory, so the block's area is dynamic (aligned here to 128 bytes).
-__global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_pml(const StepParams p, int kz)
+__global__ void __launch_bounds__(BX * BY, PML_BLOCKS) k_step_pml(const __grid_constant__ StepParams p, int kz)
 {
     extern __shared__ unsigned char nlf_dyn_smem[];
     const unsigned mis = smem_u32(nlf_dyn_smem) & 127u;
