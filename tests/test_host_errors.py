@@ -204,10 +204,12 @@ def test_grid_limits(L):
 
 def test_batch_run_arguments_are_checked_on_the_host(L):
     """nlf_batch_run refuses a batch larger than NLF_MAX_BATCH (256) or
-    without step counts before touching any context or the device."""
+    without step counts before touching any context or the device, and an
+    empty batch returns at once."""
     hs = (C.c_void_p * 257)()
     steps = (C.c_longlong * 257)()
     status = (C.c_int * 257)()
     assert L.nlf_batch_run(hs, 257, steps, None, status) == E_ARG
     assert L.nlf_batch_run(hs, 1, None, None, status) == E_ARG
     assert L.nlf_batch_run(hs, -1, steps, None, status) == E_ARG
+    assert L.nlf_batch_run(hs, 0, steps, None, status) == 0          # an empty batch is no work
