@@ -295,7 +295,10 @@ int nlf_get_field(nlf_ctx* ctx, int which, void* dst, int dst_on_device);
  * first call allocates and initialises the state like nlf_run).  The
  * polarisation histories keep their values: at time index 0 the problem then
  * starts from rest with this field (E^{-1} = P^0 = P^{-1} = 0).  Tangential E
- * on a PEC wall must be zero.  No counterpart in the paper.
+ * on a PEC wall must be zero.  A device source is read once every stream's
+ * work has finished (the call synchronises the device); the field is on the
+ * device when the call returns, so a run launched next on any stream starts
+ * from it.  No counterpart in the paper.
  * Errors: NLF_E_ARG, NLF_E_CUDA, and those of the first run's set-up. */
 int nlf_set_field(nlf_ctx* ctx, int which, const void* src, int src_on_device);
 
@@ -338,9 +341,11 @@ long long nlf_num_records(const nlf_ctx* ctx);
 
 /* Checkpoint: copy the whole device state (nlf_state_bytes bytes, including
  * the step counter and pending DFT samples) to / from host memory.  Both
- * allocate and initialise the state first if no run has done so.  The paper
- * has no counterpart (its runs of 3e5 and 4e5 iterations, Sec. V and VI, are
- * the case for one).  Errors: NLF_E_ARG, NLF_E_CUDA. */
+ * allocate and initialise the state first if no run has done so, wait for
+ * the context's stream and return once the copy has completed (a run
+ * launched after nlf_load_state on any stream starts from the loaded
+ * state).  The paper has no counterpart (its runs of 3e5 and 4e5
+ * iterations, Sec. V and VI, are the case for one).  Errors: NLF_E_ARG, NLF_E_CUDA. */
 int nlf_save_state(nlf_ctx* ctx, void* host);
 int nlf_load_state(nlf_ctx* ctx, const void* host);
 
@@ -353,7 +358,9 @@ int nlf_load_state(nlf_ctx* ctx, const void* host);
  * buffered, as after nlf_run, until the next flush or nlf_get_spectra), and
  * the rest one context at a time.  status_out[i] receives each context's
  * status (NLF_OK or NLF_E_*).  All contexts must be configured; contexts with
- * a plane monitor are refused (NLF_E_ARG).  The paper has no counterpart
+ * a plane monitor are refused (NLF_E_ARG).  A set of contexts met for the
+ * first time gets its launch descriptors copied on `cuda_stream`, and the
+ * call waits for that stream there (any stream, blocking or not, is safe).  The paper has no counterpart
  * (it runs one problem per MPI job). */
 int nlf_batch_run(nlf_ctx** ctxs, int n, const long long* steps, void* cuda_stream, int* status_out);
 

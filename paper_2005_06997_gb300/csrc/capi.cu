@@ -1131,8 +1131,9 @@ int plan_alive(BatchPlan* P)
 }
 const int kTuneKz[] = {8, 16, 32};
 
-// Build the device descriptors of a plan for z chunk kz (0: heuristic).
-int plan_descriptors(BatchPlan* P, int kz)
+// Build the device descriptors of a plan for z chunk kz (0: heuristic),
+// copied on st, the stream its launches go to.
+int plan_descriptors(BatchPlan* P, int kz, cudaStream_t st)
 {
     nlf_ctx* c = P->ctxs[0];
     const int n = (int)P->ctxs.size();
@@ -1225,7 +1226,12 @@ int plan_descriptors(BatchPlan* P, int kz)
     memcpy(h.data() + o_rec, rec_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_ph, ph_end.data(), n * sizeof(long long));
     memcpy(h.data() + o_ch, chunk_end.data(), n * sizeof(long long));
-    CK(cudaMemcpy(P->dev, h.data(), o, cudaMemcpyHostToDevice));
+    // a plain cudaMemcpy from pageable memory goes to the legacy stream and may
+    // return before its DMA lands, unordered with launches on a non-blocking
+    // stream: copy on st and wait, so that no launch can read the descriptors
+    // of an earlier plan that this allocation reuses
+    CK(cudaMemcpyAsync(P->dev, h.data(), o, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     P->bs.params = reinterpret_cast<const nlf::StepParams*>(P->dev + o_par);
     P->bs.inst = reinterpret_cast<const nlf::BatchInst*>(P->dev + o_inst);
     P->bs.item_end = reinterpret_cast<const long long*>(P->dev + o_item);
@@ -1322,7 +1328,7 @@ double inst_cost(const nlf_ctx* c)
 
 int g_kz_best = 0;                    // z chunk chosen by the autotuner (0: not tuned yet)
 
-BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
+BatchPlan* find_plan(std::vector<nlf_ctx*> act, cudaStream_t st, int* rcode)
 {
     std::stable_sort(act.begin(), act.end(),
                      [](const nlf_ctx* a, const nlf_ctx* b) { return inst_cost(a) > inst_cost(b); });
@@ -1348,7 +1354,7 @@ BatchPlan* find_plan(std::vector<nlf_ctx*> act, int* rcode)
             return nullptr;
         }
     }
-    *rcode = plan_descriptors(P.get(), g_kz_best);
+    *rcode = plan_descriptors(P.get(), g_kz_best, st);
     if (*rcode) return nullptr;
     g_plans.push_back(std::move(P));
     return g_plans.back().get();
@@ -1364,14 +1370,14 @@ int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     int rcode = NLF_OK;
-    BatchPlan* P = find_plan(act, &rcode);
+    BatchPlan* P = find_plan(act, st, &rcode);
     if (!P) return rcode;
     if ((rcode = plan_alive(P))) return rcode;
     nlf_ctx* c = P->ctxs[0];
     const int ncand = (int)(sizeof(kTuneKz) / sizeof(kTuneKz[0]));
     if (g_kz_best == 0) {
         const int kz = kTuneKz[P->tried.size() % ncand];
-        if ((rcode = plan_descriptors(P, kz))) return rcode;
+        if ((rcode = plan_descriptors(P, kz, st))) return rcode;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -1391,7 +1397,7 @@ int batch_segment(const std::vector<nlf_ctx*>& act, cudaStream_t st)
             for (size_t q = 1; q < P->tried.size(); ++q)
                 if (P->tried_ms[q] < P->tried_ms[best]) best = q;
             g_kz_best = P->tried[best];
-            if ((rcode = plan_descriptors(P, g_kz_best))) return rcode;
+            if ((rcode = plan_descriptors(P, g_kz_best, st))) return rcode;
         }
     } else if (P->uses == 0) {
         c->launches += plan_launch(P, st);
@@ -1414,7 +1420,7 @@ int batch_tail(const std::vector<nlf_ctx*>& act, int steps, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     int rcode = NLF_OK;
-    BatchPlan* P = find_plan(act, &rcode);
+    BatchPlan* P = find_plan(act, st, &rcode);
     if (!P) return rcode;
     if ((rcode = plan_alive(P))) return rcode;
     if (steps <= 0 || steps >= P->U) return NLF_E_ARG;
@@ -1523,8 +1529,11 @@ int nlf_set_material_map(nlf_ctx* c, const uint8_t* ids3, int on_device)
     if (!c || !ids3) return NLF_E_ARG;
     if (c->ready) return fail(c, NLF_E_STATE, "geometry is fixed after the first run");
     if (on_device) {
-        // the map is planned on the host (bounding box, id checks): copy it over
+        // the map is planned on the host (bounding box, id checks): copy it
+        // over once every stream's work has finished (the caller may have
+        // written it on a stream that a legacy-stream copy does not wait for)
         std::vector<uint8_t> h(3 * (size_t)c->ncell);
+        CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(h.data(), ids3, h.size(), cudaMemcpyDeviceToHost));
         c->d2h += (long long)h.size();
         c->map.swap(h);
@@ -1828,7 +1837,12 @@ int nlf_get_field(nlf_ctx* c, int which, void* dst, int on_device)
                     full[((size_t)(bk + c->bb_lo[2]) * c->g.ny + (bj + c->bb_lo[1])) * c->g.nx + bi + c->bb_lo[0]] =
                         (float)(kEps0 * sub[((size_t)bk * c->bb_n[1] + bj) * c->bb_n[0] + bi]);
     }
-    CK(cudaMemcpy(dst, full.data(), n * sizeof(float), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    if (on_device) {
+        CK(cudaMemcpyAsync(dst, full.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        memcpy(dst, full.data(), n * sizeof(float));
+    }
     return NLF_OK;
 }
 
@@ -1848,7 +1862,10 @@ int nlf_set_field(nlf_ctx* c, int which, const void* src, int src_on_device)
     std::vector<float> h;
     const float* from = static_cast<const float*>(src);
     if (src_on_device) {
+        // the source may have been written on any stream (see
+        // nlf_set_material_map)
         h.resize(n);
+        CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(h.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
         from = h.data();
     }
@@ -1857,8 +1874,10 @@ int nlf_set_field(nlf_ctx* c, int which, const void* src, int src_on_device)
         for (size_t q = 0; q < n; ++q) h[q] = (float)(h[q] * c->eta0);
         from = h.data();
     }
-    CK(cudaMemcpy2D(dst, (size_t)c->px * sizeof(float), from, (size_t)c->g.nx * sizeof(float),
-                    (size_t)c->g.nx * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice));
+    // on the context's stream, waited for (see nlf_load_state)
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->px * sizeof(float), from, (size_t)c->g.nx * sizeof(float),
+                         (size_t)c->g.nx * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     c->h2d += (long long)(n * sizeof(float));
     return NLF_OK;
 }
@@ -1966,12 +1985,18 @@ int nlf_load_state(nlf_ctx* c, const void* host)
     if (!c || !host) return NLF_E_ARG;
     int rc = ensure_ready(c, c->stream);
     if (rc) return rc;
-    CK(cudaStreamSynchronize(c->stream));
-    CK(cudaMemcpy(c->base, host, c->bytes, cudaMemcpyHostToDevice));
+    // copies on the context's stream, waited for: later launches on any
+    // stream read the loaded state (a plain cudaMemcpy from pageable memory
+    // may return before its DMA lands)
+    cudaStream_t st = c->stream;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(c->base, host, c->bytes, cudaMemcpyHostToDevice, st));
     // the tensor maps hold this buffer's addresses, not the saved state's,
     // and the header this context's id
-    CK(cudaMemcpy(c->base + c->off_tmap, c->tmaps, sizeof c->tmaps, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->base + c->off_hdr + offsetof(Header, ctx_id), &c->id, sizeof c->id, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c->base + c->off_tmap, c->tmaps, sizeof c->tmaps, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->base + c->off_hdr + offsetof(Header, ctx_id), &c->id, sizeof c->id,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     Header h{};
     memcpy(&h, host, sizeof h);
     c->n = h.n;

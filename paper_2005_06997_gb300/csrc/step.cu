@@ -824,11 +824,12 @@ __device__ __forceinline__ void march_tma(const StepParams& p, int x0, int y0, i
         for (int q = 0; q < NE; ++q) mbar_init(&sm.barE[q]);
         for (int q = 0; q < NH; ++q) mbar_init(&sm.barH[q]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        // maps read from the state were written to device memory by a copy,
-        // not by this proxy (maps in the kernel parameter need no fence)
+        // maps read from the state were written to device memory by a copy
+        // from the host, not by this proxy: the acquire takes system scope
+        // (maps in the kernel parameter need no fence)
         if (!p.map_in_params) {
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmE) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(p.tmH) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;\n" ::"l"(p.tmE) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;\n" ::"l"(p.tmH) : "memory");
         }
     }
     __syncthreads();

@@ -144,3 +144,90 @@ def test_batched_edge_geometries_match_oracle():
         ref = {c: o.array(c) for comps in VECTORS.values() for c in comps}
         errs = vec_err(fields(s), ref)
         assert max(errs.values()) <= 1e-4, (p["shape"], errs)
+
+
+def _busy_copy_engines(torch, side, mb=256, rounds=8):
+    """Queue `rounds` pinned host-to-device copies of `mb` MB on stream `side`
+    (keeps the copy engines busy while other streams launch work)."""
+    host = torch.empty(mb << 20, dtype=torch.uint8).pin_memory()
+    dev = torch.empty(mb << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(side):
+        for _ in range(rounds):
+            dev.copy_(host, non_blocking=True)
+    return host, dev
+
+
+def test_batched_plans_on_a_non_blocking_stream_with_busy_copy_engines():
+    """Batched plans made and launched on a non-blocking stream (a torch
+    stream, as the server's lanes use) while another stream keeps the copy
+    engines busy: every new plan's descriptors are on the device before its
+    first launch, so the fields equal those of the same batch on the legacy
+    default stream.  The member set shrinks every DFT period, so each period
+    makes a new plan."""
+    torch = pytest.importorskip("torch")
+    probs = instances(4, 0, nf=8)
+    b = 8
+    U = 16 * b
+    steps = [4 * U, 3 * U, 2 * U, U]
+    ref = [nlfdtd.Solver(p, block_b=b) for p in probs]
+    assert nlfdtd.batch_run(ref, steps) == [0] * 4
+    ref_f = [fields(s) for s in ref]
+    runs = [nlfdtd.Solver(p, block_b=b) for p in probs]
+    lane, side = torch.cuda.Stream(), torch.cuda.Stream()
+    keep = _busy_copy_engines(torch, side)
+    status = nlfdtd.batch_run(runs, steps, lane.cuda_stream)
+    side.synchronize()
+    del keep
+    assert status == [0] * 4
+    for q, (s, f) in enumerate(zip(runs, ref_f)):
+        s.sync()
+        assert s.n == steps[q]
+        errs = vec_err(fields(s), f)
+        assert max(errs.values()) <= 1e-6, (q, errs)
+
+
+def test_state_and_field_writes_land_before_a_run_on_a_non_blocking_stream():
+    """nlf_load_state and nlf_set_field copy on the context's stream (here
+    the legacy default stream) and wait: a run launched right after on a
+    non-blocking stream, with the copy engines busy, starts from the loaded
+    state and the set field."""
+    torch = pytest.importorskip("torch")
+    p = instances(1, 0, nf=8)[0]
+    a = nlfdtd.Solver(p)
+    a.run(300)
+    a.sync()
+    snap = a.save_state()
+    ex = a.field("Ex")
+    a.run(200)
+    a.sync()
+    ref = fields(a)
+    lane, side = torch.cuda.Stream(), torch.cuda.Stream()
+    s = nlfdtd.Solver(p)
+    s.run(0)                                   # state initialised on the legacy stream
+    keep = _busy_copy_engines(torch, side)
+    s.load_state(snap)
+    s.run(200, lane.cuda_stream)
+    s.sync()
+    side.synchronize()
+    errs = vec_err(fields(s), ref)
+    assert max(errs.values()) <= 1e-7, errs
+    # the same with E_x written over the loaded state: a changed field is seen
+    c = nlfdtd.Solver(p)
+    c.run(0)
+    c.load_state(snap)
+    c.set_field("Ex", 2.0 * ex)
+    c.run(200)
+    c.sync()
+    ref2 = fields(c)
+    t = nlfdtd.Solver(p)
+    t.run(0)
+    t.load_state(snap)
+    keep2 = _busy_copy_engines(torch, side)
+    t.set_field("Ex", 2.0 * ex)
+    t.run(200, lane.cuda_stream)
+    t.sync()
+    side.synchronize()
+    del keep, keep2
+    errs = vec_err(fields(t), ref2)
+    assert max(errs.values()) <= 1e-7, errs
+    assert vec_err(ref2, ref)["E"] > 1e-3          # the set field changed the run
