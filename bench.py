@@ -27,11 +27,14 @@ GNOR sphere with a Lorentz pole (8000 steps) is reported beside it under
            byte count of one time step (fields, hydrodynamic state, CPML,
            material ids, running DFT)
   cpu_baseline - the FP64 CPU oracle on a bounded sample of the same workload
-  serving - (with --serving N) solves/s and p50/p99 latency of the seeded
-           256-request stream, continuous batching against one grid at a
-           time, at the stated 20 req/s and at 0.7 of the plain form's
-           capacity; off by default (the full stream adds about five and a
-           half minutes)
+  serving - solves/s and p50/p99 latency of the seeded request stream's
+           first N requests (--serving N; default 128 on one GPU, none under
+           torchrun), continuous batching against one grid at a time, at the
+           stated 20 req/s and at 0.7 of the plain form's capacity; run in a
+           child process after the other sections (a failure there is
+           reported in the section and leaves the line intact); the whole
+           256-request stream (--serving 256) takes about five and a half
+           minutes
   batched - the 64-instance batched configuration (uneven 40^3..128^3 grids,
            4000 time steps each) advanced together by nlf_batch_run, against
            the same solves run one grid per launch sequence (wall time)
@@ -462,8 +465,14 @@ def run_ours(args, rank, world, dist):
     second = None
     if not args.headline_only:
         second = measure(SECOND, max(args.steps, 5), max(args.warmup, 3), dist, dev, stream, e2e_reps=3)
-    serving = run_serving(args.serving) if args.serving > 0 else None
     batched = run_batched(args.batched) if args.batched > 0 else None
+    n_serve = args.serving if args.serving >= 0 else (128 if world == 1 else 0)
+    serving = None
+    if n_serve > 0 and rank == 0:
+        # the child gets the device memory this process no longer needs
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        serving = run_serving_child(n_serve)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -536,6 +545,21 @@ def run_serving(n):
     out["load_0p7"] = {"rate_req_per_s": rate, "of": "fifo capacity", "batched": {k: sb7[k] for k in keys},
                        "fifo": {k: sf7[k] for k in keys}}
     return out
+
+
+def run_serving_child(n, timeout_s=900):
+    """run_serving(n) in a child process: its section of the line, or the
+    reason it has none."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serving-child", str(n)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"requests": n, "error": "no result within %d s" % timeout_s}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        tail = (r.stderr.strip().splitlines() or ["no output"])[-1]
+        return {"requests": n, "error": "exit %d: %s" % (r.returncode, tail[:300])}
+    return json.loads(lines[-1])
 
 
 def run_batched(n):
@@ -620,10 +644,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="skip the 224^3 section")
-    # the serving stream is opt-in: its full 256-request run takes minutes
-    ap.add_argument("--serving", type=int, default=0, help="requests of the serving stream to run (0: skip)")
+    ap.add_argument("--serving", type=int, default=-1,
+                    help="requests of the serving stream to run (0: skip; default 128 on one GPU, 0 under torchrun)")
+    ap.add_argument("--serving-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--batched", type=int, default=64, help="instances of the batched configuration (0: skip)")
     args = ap.parse_args()
+    if args.serving_child > 0:
+        # the serving section's child process (the library is already built)
+        print(json.dumps(run_serving(args.serving_child)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
