@@ -262,7 +262,11 @@ int nlf_bind_state(nlf_ctx* ctx, void* dev_ptr, size_t bytes);
  * decimate_k steps, the running DFT.  Asynchronous; the first call validates
  * the geometry (nonlocal metal only inside the total-field region, Sec. III),
  * allocates (unless bound), voxelises and uploads.  Runs are
- * resumable: run(a) then run(b) equals run(a+b) bit for bit.
+ * resumable: run(a) then run(b) equals run(a+b) bit for bit.  The calls
+ * that read results, save, destroy or wait (nlf_get_*, nlf_save_state,
+ * nlf_sync, nlf_destroy) order themselves after the context's last stream;
+ * a caller that moves one context to another stream orders the two streams
+ * itself (an event between them, or a synchronisation).
  * Errors: NLF_E_STATE, NLF_E_GEOMETRY, NLF_E_OOM, NLF_E_CUDA. */
 int nlf_run(nlf_ctx* ctx, long long steps, void* cuda_stream);
 
