@@ -133,3 +133,34 @@ def test_request_larger_than_the_budget_is_refused():
     assert by_name[reqs[big]["name"]]["status"] == -4        # NLF_E_OOM
     assert summary["solves"] == len(reqs) - 1
     assert srv.used == 0
+
+
+def test_two_lanes_side_by_side_equal_alone_results(monkeypatch):
+    """With fill_cells set so that about half of the requests count as large,
+    the large lane (one grid at a time through nlf_run) and the small lane
+    (batches through nlf_batch_run) run side by side on two non-blocking
+    streams while requests come and go, each lane making new batched plans
+    and graphs as its member set changes: every served result equals the
+    request solved alone."""
+    reqs = small_requests(10, spread_s=0.02)
+    fill = 4.4e5
+    n_large = sum(1 for q in reqs if np.prod(q["shape"]) > fill / 2)
+    assert 3 <= n_large <= 7
+    sizes = []
+    orig = nlfdtd.batch_run
+
+    def batch_run(solvers, steps, stream=None):
+        sizes.append(len(solvers))
+        return orig(solvers, steps, stream)
+
+    monkeypatch.setattr(nlfdtd, "batch_run", batch_run)
+    srv = serve.Server(hbm_budget_bytes=64 << 30, fill_cells=fill)
+    results, summary = srv.run(reqs)
+    assert summary["solves"] == len(reqs)
+    assert max(sizes) >= 2                       # the small lane batched
+    by_name = {r["name"]: r for r in results}
+    for q in reqs:
+        r = by_name[q["name"]]
+        assert r["status"] == 0
+        assert_close(r["spectra"], alone_spectra(q))
+    assert srv.used == 0
