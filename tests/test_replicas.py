@@ -42,3 +42,34 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.replica_time_ms(42.0, None, "cpu") == 42.0
     assert bench.replica_value(1, 5.0e9, 1000.0) == pytest.approx(5.0)
+
+
+def test_serving_child_failure_is_reported_in_its_section(monkeypatch):
+    """The benchmark's serving section runs in a child process: a child that
+    fails or runs out of time leaves a section that says so, and a child
+    that succeeds hands over its JSON line."""
+    import subprocess
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def timeout(cmd, **kw):
+        raise subprocess.TimeoutExpired(cmd, kw.get("timeout"))
+
+    monkeypatch.setattr(bench.subprocess, "run", timeout)
+    out = bench.run_serving_child(16, timeout_s=5)
+    assert out == {"requests": 16, "error": "no result within 5 s"}
+
+    def crash(cmd, **kw):
+        assert "--serving-child" in cmd and "16" in cmd
+        return types.SimpleNamespace(returncode=1, stdout="", stderr="line one\nRuntimeError: no device\n")
+
+    monkeypatch.setattr(bench.subprocess, "run", crash)
+    out = bench.run_serving_child(16)
+    assert out["requests"] == 16 and out["error"] == "exit 1: RuntimeError: no device"
+
+    def ok(cmd, **kw):
+        return types.SimpleNamespace(returncode=0, stdout='note\n{"requests": 16, "batched": {}}\n', stderr="")
+
+    monkeypatch.setattr(bench.subprocess, "run", ok)
+    assert bench.run_serving_child(16) == {"requests": 16, "batched": {}}
