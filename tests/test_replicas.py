@@ -1,6 +1,7 @@
-"""The multi-GPU form is replicas only: each rank solves its own grid and the
-job time is the slowest rank's.  The aggregation bench.py uses, checked with
-two gloo ranks on CPU."""
+"""Host logic of bench.py.  The multi-GPU form is replicas only: each rank
+solves its own grid and the job time is the slowest rank's (the aggregation
+checked with two gloo ranks on CPU); the serving section's child process
+reports its failures in the section."""
 import os
 import sys
 
